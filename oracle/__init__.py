@@ -1,0 +1,245 @@
+"""ORACLE — test infrastructure only.
+
+Plain single-threaded FP64 C restatement of the VELOCIraptor substructure hot path
+(Elahi et al. 2019, Sec. 2.1-2.2), used to check the CUDA library. Only ``tests/``,
+``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may load it. It shares
+no code with the CUDA library; both consume the arrays written by ``synth``.
+
+The C source is ``oracle.c`` (compiled with -O2 -ffp-contract=off, so no fused
+multiply-add changes its rounding). This module compiles it on first use and wraps
+each entry point for numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OR_HS = 12  # per-halo row of pipeline(): see HALO_COLS
+HALO_COLS = ("label", "nh", "searched", "Rbar", "sigR", "vfx", "vfy", "vfz", "sigma_host",
+             "lx2", "lv2", "ncells")
+
+
+def build(force: bool = False) -> str:
+    with _lock:
+        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+            tmp = _LIB + f".{os.getpid()}.tmp"
+            subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                                   "-shared", "-std=gnu11", _SRC, "-o", tmp, "-lm"])
+            os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Params(ctypes.Structure):
+    """Search parameters with the paper's defaults (Table 1; Table A1)."""
+
+    _fields_ = [
+        ("nse", ctypes.c_int32), ("nv", ctypes.c_int32), ("f_cell", ctypes.c_double),
+        ("ncell_min", ctypes.c_int32), ("nmin", ctypes.c_int32), ("nsearch_min", ctypes.c_int32),
+        ("ell_th", ctypes.c_double), ("v_ratio", ctypes.c_double), ("theta_op", ctypes.c_double),
+        ("use_lv", ctypes.c_int32), ("use_vr_theta", ctypes.c_int32),
+        ("split_rule", ctypes.c_int32), ("fit_nbins_min", ctypes.c_int32),
+        ("fit_nbins_max", ctypes.c_int32), ("fit_iters", ctypes.c_int32),
+    ]
+
+    @classmethod
+    def default(cls, **kw) -> "Params":
+        p = cls(nse=256, nv=32, f_cell=0.01, ncell_min=100, nmin=20, nsearch_min=160,
+                ell_th=2.5, v_ratio=2.0, theta_op=0.1 * math.pi, use_lv=1, use_vr_theta=1,
+                split_rule=0, fit_nbins_min=10, fit_nbins_max=200, fit_iters=100)
+        for k, v in kw.items():
+            setattr(p, k, v)
+        return p
+
+
+def _lib_():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+        sig = {
+            "or_fof3d": (ctypes.c_int, [vp, i64, i64, vp]),
+            "or_fof3d_brute": (ctypes.c_int, [vp, i64, i64, vp]),
+            "or_halos": (i64, [vp, i64, i32, vp, vp]),
+            "or_unwrap": (None, [vp, vp, i64, vp]),
+            "or_velden_halo": (ctypes.c_int, [vp, vp, vp, i64, ctypes.c_int, ctypes.c_int, vp]),
+            "or_velden_one": (dbl, [vp, vp, vp, i64, i64, ctypes.c_int, ctypes.c_int]),
+            "or_knn_one": (i64, [vp, vp, i64, i64, ctypes.c_int, vp]),
+            "or_ncell": (i64, [i64, dbl, i32]),
+            "or_ln_fbg": (dbl, [vp, vp, vp]),
+            "or_background_halo": (i64, [vp, vp, vp, i64, vp, dbl, i32, ctypes.c_int, vp, vp, vp]),
+            "or_ell_fit": (ctypes.c_int, [vp, i64, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp]),
+            "or_fof6d_halo": (ctypes.c_int, [vp, vp, vp, i64, vp, vp, dbl, dbl, ctypes.c_int,
+                                             ctypes.c_int, i32, vp]),
+            "or_halo_frame": (None, [vp, vp, i64, vp]),
+            "or_pipeline": (i64, [vp, vp, i64, i64, dbl, dbl, ctypes.POINTER(Params), vp, vp, vp,
+                                  vp, vp, vp]),
+            "or_ell_bar": (dbl, [dbl]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data if a is not None else None
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+# ------------------------------------------------------------------- wrappers
+
+def fof3d(pos, link_d2: int, brute: bool = False) -> np.ndarray:
+    """3D FOF labels (minimum index per group), Eq. fof3d."""
+    pos = _c(pos, np.int32)
+    n = pos.shape[0]
+    lab = np.empty(n, np.int32)
+    f = _lib_().or_fof3d_brute if brute else _lib_().or_fof3d
+    rc = f(_p(pos), n, int(link_d2), _p(lab))
+    if rc != 0:
+        raise RuntimeError(f"oracle fof3d failed ({rc})")
+    return lab
+
+
+def halos(label, nmin: int):
+    """(offsets[H+1], members) of groups with >= nmin members, members increasing."""
+    label = _c(label, np.int32)
+    n = label.shape[0]
+    L = _lib_()
+    H = L.or_halos(_p(label), n, nmin, None, None)
+    if H < 0:
+        raise ValueError("bad labels")
+    off = np.empty(H + 1, np.int64)
+    mem = np.empty(max(n, 1), np.int32)
+    L.or_halos(_p(label), n, nmin, _p(off), _p(mem))
+    return off, mem[: off[-1]].copy()
+
+
+def unwrap(pos, members) -> np.ndarray:
+    pos = _c(pos, np.int32)
+    members = _c(members, np.int32)
+    up = np.empty((members.shape[0], 3), np.int64)
+    _lib_().or_unwrap(_p(pos), _p(members), members.shape[0], _p(up))
+    return up
+
+
+def velden_halo(upos, vel, members, nse=256, nv=32) -> np.ndarray:
+    upos = _c(upos, np.int64)
+    vel = _c(vel, np.float32)
+    members = _c(members, np.int32)
+    out = np.empty(members.shape[0], np.float64)
+    rc = _lib_().or_velden_halo(_p(upos), _p(vel), _p(members), members.shape[0], nse, nv, _p(out))
+    if rc != 0:
+        raise RuntimeError(f"oracle velden failed ({rc})")
+    return out
+
+
+def velden_one(upos, vel, members, k: int, nse=256, nv=32) -> float:
+    upos = _c(upos, np.int64)
+    vel = _c(vel, np.float32)
+    members = _c(members, np.int32)
+    return _lib_().or_velden_one(_p(upos), _p(vel), _p(members), members.shape[0], k, nse, nv)
+
+
+def knn_one(upos, members, k: int, nse=256) -> np.ndarray:
+    upos = _c(upos, np.int64)
+    members = _c(members, np.int32)
+    out = np.empty(min(nse, members.shape[0]), np.int32)
+    m = _lib_().or_knn_one(_p(upos), _p(members), members.shape[0], k, nse, _p(out))
+    return out[:m]
+
+
+def ncell(nh: int, f_cell=0.01, ncell_min=100) -> int:
+    return int(_lib_().or_ncell(nh, f_cell, ncell_min))
+
+
+def ln_fbg(v, vbar, sig6) -> float:
+    v = _c(v, np.float64)
+    vbar = _c(vbar, np.float64)
+    sig6 = _c(sig6, np.float64)
+    return _lib_().or_ln_fbg(_p(v), _p(vbar), _p(sig6))
+
+
+def background_halo(upos, vel, members, f_l, f_cell=0.01, ncell_min=100, split_rule=0):
+    """Returns (R [nh], leaf_of [nh], cell_stats [nleaves, 13])."""
+    upos = _c(upos, np.int64)
+    vel = _c(vel, np.float32)
+    members = _c(members, np.int32)
+    f_l = _c(f_l, np.float64)
+    nh = members.shape[0]
+    R = np.empty(nh, np.float64)
+    leaf = np.empty(nh, np.int32)
+    cs = np.empty((max(nh, 1), 13), np.float64)
+    nl = _lib_().or_background_halo(_p(upos), _p(vel), _p(members), nh, _p(f_l), f_cell,
+                                    ncell_min, split_rule, _p(R), _p(leaf), _p(cs))
+    if nl < 0:
+        raise RuntimeError("oracle background failed")
+    return R, leaf, cs[:nl].copy()
+
+
+def ell_fit(R, nbins_min=10, nbins_max=200, iters=100) -> np.ndarray:
+    """(Rbar, sigma_R, s, A, lo, width, nbins, MAD')."""
+    R = _c(R, np.float64)
+    out = np.empty(8, np.float64)
+    _lib_().or_ell_fit(_p(R), R.shape[0], nbins_min, nbins_max, iters, _p(out))
+    return out
+
+
+def fof6d_halo(upos, vel, members, cand, prm, v_ratio=2.0, theta_op=0.1 * math.pi, use_lv=1,
+               use_vt=1, nmin=20) -> np.ndarray:
+    upos = _c(upos, np.int64)
+    vel = _c(vel, np.float32)
+    members = _c(members, np.int32)
+    cand = _c(cand, np.uint8)
+    prm = _c(prm, np.float64)
+    out = np.empty(members.shape[0], np.int32)
+    _lib_().or_fof6d_halo(_p(upos), _p(vel), _p(members), members.shape[0], _p(cand), _p(prm),
+                          v_ratio, theta_op, use_lv, use_vt, nmin, _p(out))
+    return out
+
+
+def halo_frame(vel, members) -> np.ndarray:
+    vel = _c(vel, np.float32)
+    members = _c(members, np.int32)
+    out = np.empty(4, np.float64)
+    _lib_().or_halo_frame(_p(vel), _p(members), members.shape[0], _p(out))
+    return out
+
+
+def ell_bar(ell_th: float) -> float:
+    return _lib_().or_ell_bar(ell_th)
+
+
+def pipeline(pos, vel, link_d2: int, lx_sub: float, alpha_lv: float = 1.0, params=None):
+    """Full oracle pass. Returns dict of per-particle arrays and the per-halo table."""
+    pos = _c(pos, np.int32)
+    vel = _c(vel, np.float32)
+    n = pos.shape[0]
+    P = params or Params.default()
+    lab3 = np.empty(n, np.int32)
+    fl = np.empty(n, np.float64)
+    R = np.empty(n, np.float64)
+    ell = np.empty(n, np.float64)
+    lab6 = np.empty(n, np.int32)
+    hs = np.empty((n // max(P.nmin, 1) + 1, OR_HS), np.float64)
+    H = _lib_().or_pipeline(_p(pos), _p(vel), n, int(link_d2), lx_sub, alpha_lv, ctypes.byref(P),
+                            _p(lab3), _p(fl), _p(R), _p(ell), _p(lab6), _p(hs))
+    if H < 0:
+        raise RuntimeError("oracle pipeline failed")
+    return dict(label3=lab3, f_l=fl, R=R, ell=ell, label6=lab6, halos=hs[:H].copy())
