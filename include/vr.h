@@ -1,0 +1,208 @@
+/*
+ * vr.h — C ABI of the GB300 (sm_103a) VELOCIraptor substructure hot path.
+ *
+ * Method: Elahi et al. 2019, "Hunting for Galaxies and Halos in simulations with
+ * VELOCIraptor", Sec. 2.1 (field halos, Eq. fof3d) and Sec. 2.2 (subhalos and streams:
+ * local velocity density, background model Eqs. fvbg, S, meanpos-meandispvel,
+ * cellinterp, log ratio R, skew-Gaussian fit Eqs. skewgaus/ell, phase-space linking
+ * Eq. linkingcriteria with the 6D term of Eq. fof6d).
+ *
+ * Conventions for every call:
+ *  - All array arguments are DEVICE pointers owned by the caller. Inputs are never
+ *    modified. Particle arrays are indexed by particle index i in [0, n), n < 2^31.
+ *  - Positions are int32 [n][3] (x, y, z interleaved) on a periodic lattice of 2^21
+ *    points per axis, values in [0, 2^21). Velocities are float32 [n][3] (km/s).
+ *  - Every call is asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream) and returns a vr_status. Argument errors are detected before any work is
+ *    enqueued. Device-side errors (unsupported geometry detected in a kernel) are
+ *    reported by the NEXT call that synchronises (vr_sync or a call that reads sizes
+ *    back), through its status and vr_last_error().
+ *  - Scratch memory comes from the caller's workspace `ws` of `ws_bytes` bytes (device
+ *    memory, 256-byte aligned); vr_workspace_size() gives the bytes needed for n
+ *    particles. No call allocates device memory. Calls that share a workspace must be
+ *    ordered on one stream.
+ *  - Labels are canonical: the minimum particle index of the group.
+ *  - A context (vr_ctx) holds pinned host staging for small read-backs and the last
+ *    error string; it is not thread-safe (one host thread per context).
+ */
+#ifndef VR_H
+#define VR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  VR_OK = 0,
+  VR_ERR_INVALID_ARG = 1,        /* bad pointer, size or parameter */
+  VR_ERR_CUDA = 2,               /* a CUDA runtime call failed */
+  VR_ERR_WORKSPACE_TOO_SMALL = 3,/* ws_bytes < vr_workspace_size() */
+  VR_ERR_TIMEOUT = 4,            /* a bounded device wait gave up */
+  VR_ERR_DEGENERATE_CELL = 5,    /* reserved: reported as a count, never returned */
+  VR_ERR_UNSUPPORTED = 6         /* geometry outside the supported envelope */
+} vr_status;
+
+typedef struct vr_ctx vr_ctx;
+
+/* Search parameters. Defaults (vr_params_default) are the paper's (Table 1):
+ * N_se = 256, N_v = 32, f_cell = 0.01, ell_th = 2.5, V_r = 2, Theta_op = 0.1 pi,
+ * N_min = 20; the remaining fields fix readings the paper leaves open. */
+typedef struct {
+  int32_t nse;          /* N_se physical neighbours for f_l (Sec. 2.2), 1..1024 */
+  int32_t nv;           /* N_v velocity neighbours among them, 1..64, nv <= nse */
+  double f_cell;        /* background cell size as a fraction of N_H (Sec. 2.2) */
+  int32_t ncell_min;    /* cells below this are raised to min(ncell_min, N_H/8) */
+  int32_t nmin;         /* minimum group size N_min (Sec. 2.2), >= 1 */
+  int32_t nsearch_min;  /* halos with N_H >= nsearch_min are searched (default 160) */
+  double ell_th;        /* outlier threshold ell_th (Eq. linkingcriteria a) */
+  double v_ratio;       /* speed ratio V_r (Eq. linkingcriteria c) */
+  double theta_op;      /* opening angle Theta_op in radians, < pi/2 (Eq. linkingcriteria d) */
+  int32_t use_lv;       /* 1: add the velocity term dv^2/lv^2 of Eq. fof6d to the link test */
+  int32_t use_vr_theta; /* 1: apply the V_r and Theta_op criteria */
+  int32_t split_rule;   /* 0: split cells along the axis of largest entropy S; 1: smallest */
+  int32_t fit_nbins_min;/* R histogram bins: clamp(ceil(sqrt(N)), min, max) */
+  int32_t fit_nbins_max;
+  int32_t fit_iters;    /* Levenberg-Marquardt iterations for the skew-Gaussian fit */
+} vr_params;
+
+/* Per-halo output row of vr_outlier_ratio / vr_find_substructure (VR_HALO_COLS doubles,
+ * halos in increasing label order): */
+enum {
+  VR_H_LABEL = 0,   /* halo label (minimum particle index) */
+  VR_H_NH = 1,      /* N_H */
+  VR_H_SEARCHED = 2,/* 1 if N_H >= nsearch_min (background, R, ell computed) */
+  VR_H_RBAR = 3,    /* skew-Gaussian mode R-bar (Eq. skewgaus) */
+  VR_H_SIGR = 4,    /* skew-Gaussian width sigma_R */
+  VR_H_VFX = 5,     /* halo mean velocity (frame for V_r, Theta_op) */
+  VR_H_VFY = 6,
+  VR_H_VFZ = 7,
+  VR_H_SIGMA = 8,   /* sigma_host = |Sigma_halo|^(1/6) (Table A2 sigma_v) */
+  VR_H_LX2 = 9,     /* squared spatial linking length used by vr_fof6d */
+  VR_H_LV2 = 10,    /* squared velocity linking length used by vr_fof6d */
+  VR_H_NCELLS = 11, /* number of background cells */
+  VR_HALO_COLS = 12
+};
+
+/* Fills p with the defaults above. */
+void vr_params_default(vr_params *p);
+
+/* Creates a context on CUDA device `device`. *out is NULL on failure. */
+vr_status vr_create(vr_ctx **out, int device);
+void vr_destroy(vr_ctx *ctx);
+
+/* Last error message of ctx (empty string if none). Owned by ctx. */
+const char *vr_last_error(const vr_ctx *ctx);
+
+/* Bytes of workspace needed by any call below for n particles with parameters p
+ * (p may be NULL for defaults). */
+vr_status vr_workspace_size(vr_ctx *ctx, int64_t n, const vr_params *p, size_t *bytes);
+
+/* Waits for `stream` and reports device-side errors raised by earlier calls. */
+vr_status vr_sync(vr_ctx *ctx, void *stream);
+
+/* 3D friends-of-friends (Sec. 2.1, Eq. fof3d): particles i, j are linked iff their
+ * minimum-image squared separation is < link_d2 (lattice units squared; the strict
+ * inequality of Eq. fof3d; link_d2 = floor(ell_x^2) + 1 for a non-integer ell_x^2);
+ * groups are the connected components.
+ *   pos    int32 [n][3], lattice positions in [0, 2^21)
+ *   link_d2 1 <= link_d2 <= 2^38 (linking length at most 2^19 lattice units)
+ *   label  int32 [n] out: minimum particle index of i's group
+ * Errors: VR_ERR_INVALID_ARG for NULL pointers with n > 0, n < 0, n >= 2^31, or link_d2
+ * out of range. n = 0 is a no-op. */
+vr_status vr_fof3d(vr_ctx *ctx, const int32_t *pos, int64_t n, int64_t link_d2, int32_t *label,
+                   void *ws, size_t ws_bytes, void *stream);
+
+/* Local velocity density (Sec. 2.2): for every particle of a halo (3D group with at
+ * least p->nmin members), the N_se nearest members of the same halo in position (by
+ * squared separation, ties by particle index, the particle itself included,
+ * N_se_eff = min(N_se, N_H)); h = distance in velocity to the N_v-th nearest of that
+ * set; f_l = (1/N_se_eff) sum over the set of 15/(8 pi h^3)(1 - |dv|^2/h^2) for |dv| < h
+ * (Epanechnikov kernel).
+ *   label  int32 [n] 3D labels as written by vr_fof3d (canonical)
+ *   f_l    float32 [n] out: f_l in (km/s)^-3; NaN for particles outside halos
+ * Halos must span less than half the box per axis (positions are unwrapped about the
+ * halo's minimum-index member); a halo may hold at most 2^22 particles.
+ * Errors: VR_ERR_INVALID_ARG (pointers, n, parameters); VR_ERR_UNSUPPORTED (halo too
+ * large or too extended, reported at the next synchronising call). */
+vr_status vr_velden(vr_ctx *ctx, const int32_t *pos, const float *vel, int64_t n,
+                    const int32_t *label, const vr_params *p, float *f_l, void *ws,
+                    size_t ws_bytes, void *stream);
+
+/* Outlier ratio (Sec. 2.2) for halos with N_H >= p->nsearch_min: entropy kd-tree cells of
+ * N_cell = f_cell N_H particles (raised to min(ncell_min, N_H/8)), FP64 cell moments
+ * (Eqs. meanpos, meanvel, meandispvel), inverse-distance interpolation over the
+ * particle's cell and its face neighbours (Eq. cellinterp), FP64 Cholesky of the
+ * interpolated dispersion tensor, R = ln f_l - ln f_bg (Eq. fvbg); then per halo a
+ * skew-Gaussian fit of the binned R distribution (Eq. skewgaus) and
+ * ell = (R - R-bar)/sigma_R (Eq. ell).
+ *   f_l         float32 [n] from vr_velden
+ *   R, ell      float32 [n] out; NaN outside searched halos (R is NaN where the tensor is
+ *               not positive definite)
+ *   halo_stats  double [n/nmin + 1][VR_HALO_COLS] out (rows for every halo with N_H >=
+ *               nmin, in label order; columns VR_H_*; LX2/LV2 are NaN here)
+ *   nhalo       int64 host pointer out (may be NULL): number of halos written
+ * This call synchronises `stream` to read the halo count. */
+vr_status vr_outlier_ratio(vr_ctx *ctx, const int32_t *pos, const float *vel, const float *f_l,
+                           int64_t n, const int32_t *label, const vr_params *p, float *R,
+                           float *ell, double *halo_stats, int64_t *nhalo, void *ws,
+                           size_t ws_bytes, void *stream);
+
+/* Phase-space linking of outliers (Sec. 2.2, Eq. linkingcriteria; with p->use_lv the
+ * velocity term of Eq. fof6d is added): inside each halo, candidates i, j (ell >=
+ * ell_th; every member when ell is NULL) are linked iff dx^2/lx2 (+ dv^2/lv2) < 1 and,
+ * with p->use_vr_theta, 1/V_r <= |u_i|/|u_j| <= V_r and the angle between u_i and u_j is
+ * at most Theta_op, where u = v - v_frame. dx^2 is the exact squared lattice separation
+ * of the unwrapped positions; the rest is FP64 without fused multiply-add, in the order
+ * dv2 = (dvx^2 + dvy^2) + dvz^2, q = dx2/lx2 + dv2/lv2, s = (ux^2 + uy^2) + uz^2,
+ * s_i <= V_r^2 s_j, dot >= 0 and dot^2 >= (cos^2(Theta_op) s_i) s_j.
+ *   halo_params  double [H][VR_HALO_COLS] rows as written by vr_outlier_ratio, with
+ *                VR_H_LX2, VR_H_LV2 and VR_H_VF* filled in; halos whose VR_H_SEARCHED is 0
+ *                are skipped
+ *   nhalo        number of rows
+ *   label6       int32 [n] out: minimum particle index of the linked group for
+ *                candidates in groups of >= p->nmin members, -1 otherwise */
+vr_status vr_fof6d(vr_ctx *ctx, const int32_t *pos, const float *vel, const float *ell,
+                   int64_t n, const int32_t *label, const double *halo_params, int64_t nhalo,
+                   const vr_params *p, int32_t *label6, void *ws, size_t ws_bytes,
+                   void *stream);
+
+/* The substructure search of Fig. 2 (first pass) for every halo: vr_velden, then
+ * vr_outlier_ratio, then the per-halo linking lengths lx2 = lx_sub^2 and
+ * lv2 = (alpha_lv sigma_host)^2, then vr_fof6d on the outliers. Outputs as in those
+ * calls; halo_stats gets LX2/LV2 filled in. `batched` selects the launch form:
+ * 0 = one launch per stage over all halos with host-side sizing; 1 = same kernels
+ * replayed from a captured CUDA graph (sizes kept on the device). */
+vr_status vr_find_substructure(vr_ctx *ctx, const int32_t *pos, const float *vel, int64_t n,
+                               const int32_t *label, double lx_sub, double alpha_lv,
+                               const vr_params *p, int batched, float *f_l, float *R,
+                               float *ell, int32_t *label6, double *halo_stats, int64_t *nhalo,
+                               void *ws, size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------------- measurement
+ * (no counterpart in the paper: instrumentation of this library)
+ * Per-kernel device timing with CUDA events recorded on the launching stream; off by
+ * default. Kernel names: "fof_link", "velden_big", "velden_small", "halo_frame",
+ * "cells_build", "ratio", "ell_fit", "link6". */
+
+/* Enables (1) or disables (0) event timing of the named kernels for this context. */
+vr_status vr_timing_enable(vr_ctx *ctx, int enable);
+
+/* Device time in ms summed over the launches of kernel `name` recorded since the last
+ * vr_timing_reset, and the number of those launches. Waits for the recorded events. */
+vr_status vr_timing_read(vr_ctx *ctx, const char *name, double *ms, int64_t *launches);
+
+/* Drops all recorded timings. */
+vr_status vr_timing_reset(vr_ctx *ctx);
+
+/* Number of kernels this library has launched in the calling process so far (every
+ * kernel, including those of the sort and scan primitives). */
+int64_t vr_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VR_H */

@@ -1,0 +1,578 @@
+// Background velocity model and outlier ratio (Sec. 2.2).
+//
+//  k_halo_frame   one CTA per halo: FP64 mean velocity and dispersion tensor about it
+//                 (divided by N_H), sigma_host = |Sigma|^(1/6), halo table row.
+//  k_cells_build  one CTA per searched halo: entropy kd-tree (Eq. S) down to cells of at
+//                 most N_cell members, built node by node in global working arrays;
+//                 split value = element floor(n/2) of the node in (coordinate, local
+//                 index) order found by an 8-bit radix select; FP64 cell moments
+//                 (Eqs. meanpos, meanvel, meandispvel) per leaf.
+//  k_ratio        one thread per member: own cell plus the cells across its six faces
+//                 (point location by descending the tree), inverse-distance weights
+//                 (Eq. cellinterp), FP64 Cholesky, ln f_bg (Eq. fvbg), R = ln f_l - ln f_bg.
+// Readings of points the paper leaves open (fixed identically in the oracle): bins
+// n_b = max(2, floor(n^(1/3))) over [min, max] with bin = (x - min) n_b / (max - min + 1);
+// argmax S with ties within 1e-12 going to the lower axis; an axis whose split leaves
+// the left side empty is skipped for the next-best one; regions are half-open boxes;
+// a face neighbour is the leaf containing the member's position moved to lo - 1 (or hi)
+// along that axis, skipped outside the root region and counted once.
+#include <math.h>
+
+#include "halos.cuh"
+#include "vr_workspace.h"
+#include "background.cuh"
+
+namespace vr {
+
+namespace {
+
+constexpr int kTB = 256;           // threads per tree-building CTA
+constexpr int kMaxBins = 162;      // floor((2^22)^(1/3)) + 1
+
+__device__ __forceinline__ int64_t ncell_of(int64_t nh, double f_cell, int ncell_min) {
+  int64_t nc = (int64_t)floor(__dmul_rn(f_cell, (double)nh));
+  if (nc < ncell_min) {
+    nc = ncell_min;
+    if (nh / 8 < nc) nc = nh / 8;
+  }
+  return nc < 1 ? 1 : nc;
+}
+
+__device__ __forceinline__ int64_t icbrt_dev(int64_t n) {
+  int64_t m = (int64_t)cbrt((double)n);
+  while (m > 0 && m * m * m > n) --m;
+  while ((m + 1) * (m + 1) * (m + 1) <= n) ++m;
+  return m;
+}
+
+// ---- block reductions (256 threads) ----
+template <class T, class Op>
+__device__ __forceinline__ T block_reduce(T v, Op op, T *sbuf) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int o = 16; o; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if (lane == 0) sbuf[w] = v;
+  __syncthreads();
+  T r = sbuf[0];
+  for (int k = 1; k < kTB / 32; ++k) r = op(r, sbuf[k]);
+  __syncthreads();
+  return r;
+}
+
+struct MinOp { __device__ int operator()(int a, int b) const { return a < b ? a : b; } };
+struct MaxOp { __device__ int operator()(int a, int b) const { return a > b ? a : b; } };
+struct AddL { __device__ long long operator()(long long a, long long b) const { return a + b; } };
+struct AddD { __device__ double operator()(double a, double b) const { return a + b; } };
+struct AddI { __device__ int operator()(int a, int b) const { return a + b; } };
+
+__device__ __forceinline__ int coord(const int4 &p, int a) { return a == 0 ? p.x : (a == 1 ? p.y : p.z); }
+
+}  // namespace
+
+// Halo table row for every halo (searched or not): FP64 frame and sigma_host.
+__global__ void __launch_bounds__(kTB) k_halo_frame(const uint32_t *__restrict__ hoff,
+                                                    const uint32_t *__restrict__ hlabel, int64_t H,
+                                                    const float4 *__restrict__ v, int nsearch_min,
+                                                    double *__restrict__ hs_out) {
+  __shared__ double sd[kTB / 32];
+  const int64_t h = blockIdx.x;
+  if (h >= H) return;
+  const uint32_t b = hoff[h], e = hoff[h + 1];
+  const double nh = (double)(e - b);
+  double s[3] = {0, 0, 0};
+  for (uint32_t m = b + threadIdx.x; m < e; m += kTB) {
+    float4 q = v[m];
+    s[0] += (double)q.x;
+    s[1] += (double)q.y;
+    s[2] += (double)q.z;
+  }
+  double mean[3];
+  for (int k = 0; k < 3; ++k) mean[k] = block_reduce(s[k], AddD(), sd) / nh;
+  double c[6] = {0, 0, 0, 0, 0, 0};
+  for (uint32_t m = b + threadIdx.x; m < e; m += kTB) {
+    float4 q = v[m];
+    double d0 = (double)q.x - mean[0], d1 = (double)q.y - mean[1], d2 = (double)q.z - mean[2];
+    c[0] += d0 * d0; c[1] += d1 * d1; c[2] += d2 * d2;
+    c[3] += d0 * d1; c[4] += d0 * d2; c[5] += d1 * d2;
+  }
+  double S[6];
+  for (int k = 0; k < 6; ++k) S[k] = block_reduce(c[k], AddD(), sd) / nh;
+  if (threadIdx.x == 0) {
+    double det = S[0] * (S[1] * S[2] - S[5] * S[5]) - S[3] * (S[3] * S[2] - S[5] * S[4]) +
+                 S[4] * (S[3] * S[5] - S[1] * S[4]);
+    double *row = hs_out + h * VR_HALO_COLS;
+    row[VR_H_LABEL] = (double)hlabel[h];
+    row[VR_H_NH] = nh;
+    row[VR_H_SEARCHED] = (e - b) >= (uint32_t)nsearch_min ? 1.0 : 0.0;
+    row[VR_H_RBAR] = NAN;
+    row[VR_H_SIGR] = NAN;
+    row[VR_H_VFX] = mean[0];
+    row[VR_H_VFY] = mean[1];
+    row[VR_H_VFZ] = mean[2];
+    row[VR_H_SIGMA] = det > 0.0 ? pow(det, 1.0 / 6.0) : 0.0;
+    row[VR_H_LX2] = NAN;
+    row[VR_H_LV2] = NAN;
+    row[VR_H_NCELLS] = 0.0;
+  }
+}
+
+// Node-capacity bound per halo (node table slots), 0 for halos not searched.
+__global__ void k_node_caps(const uint32_t *__restrict__ hoff, int64_t H, int nsearch_min,
+                            double f_cell, int ncell_min, uint32_t *__restrict__ caps) {
+  int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (h > H) return;
+  if (h == H) {
+    caps[H] = 0;
+    return;
+  }
+  int64_t nh = hoff[h + 1] - hoff[h];
+  if (nh < nsearch_min) {
+    caps[h] = 0;
+    return;
+  }
+  int64_t nc = ncell_of(nh, f_cell, ncell_min);
+  caps[h] = (uint32_t)(kNodeFactor * ((nh + nc) / (nc + 1)) + 16);
+}
+
+__global__ void __launch_bounds__(kTB) k_cells_build(
+    const uint32_t *__restrict__ hoff, const uint32_t *__restrict__ nodeoff, int64_t H,
+    const int4 *__restrict__ u, const float4 *__restrict__ v, int nsearch_min, double f_cell,
+    int ncell_min, int split_rule, uint32_t *__restrict__ perm, uint32_t *__restrict__ tmp,
+    CellNode *__restrict__ nodes, double *__restrict__ mom, uint32_t *__restrict__ leaf_of,
+    double *__restrict__ hs_out, DevStatus *st) {
+  __shared__ int s_hist[3][kMaxBins];
+  __shared__ uint32_t s_dig[256];
+  __shared__ int s_ri[kTB / 32];
+  __shared__ long long s_rl[kTB / 32];
+  __shared__ double s_rd[kTB / 32];
+  __shared__ int s_order[3];
+  __shared__ int s_norder;
+  __shared__ unsigned long long s_prefix;
+  __shared__ int s_rank;
+  __shared__ int s_count;
+  __shared__ uint32_t s_scan[kTB];
+  const int64_t h = blockIdx.x;
+  if (h >= H) return;
+  const uint32_t hb = hoff[h], he = hoff[h + 1];
+  const int64_t nh = he - hb;
+  if (nh < nsearch_min) return;
+  const int64_t ncell = ncell_of(nh, f_cell, ncell_min);
+  const uint32_t base = nodeoff[h], cap = nodeoff[h + 1] - base;
+  const int t = threadIdx.x;
+  for (uint32_t m = hb + t; m < he; m += kTB) perm[m] = m;
+  // root region: [min, max + 1)
+  {
+    int mn[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff}, mx[3] = {-0x7fffffff, -0x7fffffff, -0x7fffffff};
+    for (uint32_t m = hb + t; m < he; m += kTB) {
+      int4 p = u[m];
+      mn[0] = min(mn[0], p.x); mn[1] = min(mn[1], p.y); mn[2] = min(mn[2], p.z);
+      mx[0] = max(mx[0], p.x); mx[1] = max(mx[1], p.y); mx[2] = max(mx[2], p.z);
+    }
+    for (int a = 0; a < 3; ++a) {
+      int lo = block_reduce(mn[a], MinOp(), s_ri);
+      int hi = block_reduce(mx[a], MaxOp(), s_ri);
+      if (t == 0) {
+        nodes[base].lo[a] = lo;
+        nodes[base].hi[a] = hi + 1;
+      }
+    }
+    if (t == 0) {
+      nodes[base].beg = hb;
+      nodes[base].end = he;
+      nodes[base].axis = -1;
+      s_count = 1;
+    }
+  }
+  __syncthreads();
+  for (int cur = 0; cur < s_count; ++cur) {
+    CellNode *nd = &nodes[base + cur];
+    const uint32_t nb_ = nd->beg, ne_ = nd->end;
+    const int64_t n = ne_ - nb_;
+    __syncthreads();
+    if (n <= ncell) {
+      if (t == 0) nd->axis = -1;
+      __syncthreads();
+      continue;
+    }
+    // extent of the node's members per axis
+    int mn[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff}, mx[3] = {-0x7fffffff, -0x7fffffff, -0x7fffffff};
+    for (uint32_t i = nb_ + t; i < ne_; i += kTB) {
+      int4 p = u[perm[i]];
+      mn[0] = min(mn[0], p.x); mn[1] = min(mn[1], p.y); mn[2] = min(mn[2], p.z);
+      mx[0] = max(mx[0], p.x); mx[1] = max(mx[1], p.y); mx[2] = max(mx[2], p.z);
+    }
+    int amin[3], amax[3];
+    for (int a = 0; a < 3; ++a) {
+      amin[a] = block_reduce(mn[a], MinOp(), s_ri);
+      amax[a] = block_reduce(mx[a], MaxOp(), s_ri);
+    }
+    const int64_t nbins = max((int64_t)2, icbrt_dev(n));
+    for (int k = t; k < 3 * kMaxBins; k += kTB) (&s_hist[0][0])[k] = 0;
+    __syncthreads();
+    for (uint32_t i = nb_ + t; i < ne_; i += kTB) {
+      int4 p = u[perm[i]];
+      for (int a = 0; a < 3; ++a) {
+        if (amax[a] > amin[a]) {
+          int64_t bin = ((int64_t)(coord(p, a) - amin[a]) * nbins) / ((int64_t)amax[a] - amin[a] + 1);
+          atomicAdd(&s_hist[a][bin], 1);
+        }
+      }
+    }
+    __syncthreads();
+    if (t == 0) {
+      double S[3];
+      int ok[3];
+      for (int a = 0; a < 3; ++a) {
+        ok[a] = amax[a] > amin[a];
+        S[a] = 0.0;
+        if (ok[a]) {
+          double s = 0.0;
+          for (int b = 0; b < nbins; ++b) {
+            int c = s_hist[a][b];
+            if (c > 0) {
+              double f = (double)c / (double)n;
+              s -= f * log(f);
+            }
+          }
+          S[a] = s / log((double)nbins);
+        }
+      }
+      int used[3] = {0, 0, 0}, no = 0;
+      for (int r = 0; r < 3; ++r) {
+        int best = -1;
+        for (int a = 0; a < 3; ++a) {
+          if (!ok[a] || used[a]) continue;
+          if (best < 0) { best = a; continue; }
+          if (split_rule == 0 ? (S[a] > S[best] + 1e-12) : (S[a] < S[best] - 1e-12)) best = a;
+        }
+        if (best < 0) break;
+        used[best] = 1;
+        s_order[no++] = best;
+      }
+      s_norder = no;
+    }
+    __syncthreads();
+    bool split_done = false;
+    const int norder = s_norder;
+    for (int r = 0; r < norder && !split_done; ++r) {
+      const int a = s_order[r];
+      const int lo_a = amin[a];
+      // radix select of the element of rank floor(n/2) by key ((x - lo) << 22 | local index)
+      int bits = 22;
+      {
+        unsigned int ext = (unsigned int)(amax[a] - lo_a);
+        while (ext) { ++bits; ext >>= 1; }
+      }
+      int ndig = (bits + 7) / 8;
+      if (t == 0) {
+        s_prefix = 0ULL;
+        s_rank = (int)(n / 2);
+      }
+      __syncthreads();
+      for (int d = ndig - 1; d >= 0; --d) {
+        s_dig[t] = 0;
+        __syncthreads();
+        const int sh = 8 * d;
+        const unsigned long long pre = s_prefix;
+        for (uint32_t i = nb_ + t; i < ne_; i += kTB) {
+          int4 p = u[perm[i]];
+          unsigned long long key = ((unsigned long long)(coord(p, a) - lo_a) << 22) | (unsigned)p.w;
+          unsigned long long hiK = (sh + 8 >= 64) ? 0ULL : (key >> (sh + 8));
+          unsigned long long hiP = (sh + 8 >= 64) ? 0ULL : (pre >> (sh + 8));
+          if (hiK == hiP) atomicAdd(&s_dig[(key >> sh) & 0xffu], 1u);
+        }
+        __syncthreads();
+        // exclusive scan of the 256 digit counts; thread t owns digit t
+        uint32_t c = s_dig[t];
+        s_scan[t] = c;
+        __syncthreads();
+        for (int o = 1; o < 256; o <<= 1) {
+          uint32_t x = t >= o ? s_scan[t - o] : 0u;
+          __syncthreads();
+          s_scan[t] += x;
+          __syncthreads();
+        }
+        uint32_t incl = s_scan[t], excl = incl - c;
+        const int rk = s_rank;
+        __syncthreads();
+        if ((int)excl <= rk && rk < (int)incl) {
+          s_prefix = pre | ((unsigned long long)t << sh);
+          s_rank = rk - (int)excl;
+        }
+        __syncthreads();
+      }
+      const int xs = lo_a + (int)(s_prefix >> 22);
+      // left = {x < xs}
+      int cl = 0;
+      for (uint32_t i = nb_ + t; i < ne_; i += kTB) cl += coord(u[perm[i]], a) < xs ? 1 : 0;
+      const int nleft = block_reduce(cl, AddI(), s_ri);
+      if (nleft == 0) continue;  // left side empty: next axis
+      // ordered partition into tmp, then back into perm
+      uint32_t offl = 0, offr = 0;
+      for (uint32_t cb = nb_; cb < ne_; cb += kTB) {
+        uint32_t i = cb + t;
+        uint32_t pm = 0;
+        int isl = 0;
+        if (i < ne_) {
+          pm = perm[i];
+          isl = coord(u[pm], a) < xs ? 1 : 0;
+        }
+        s_scan[t] = isl;
+        __syncthreads();
+        for (int o = 1; o < kTB; o <<= 1) {
+          uint32_t x = t >= o ? s_scan[t - o] : 0u;
+          __syncthreads();
+          s_scan[t] += x;
+          __syncthreads();
+        }
+        uint32_t incl = s_scan[t];
+        uint32_t totl = s_scan[kTB - 1];
+        uint32_t cnt = min((uint32_t)kTB, ne_ - cb);
+        if (i < ne_) {
+          if (isl) tmp[nb_ + offl + incl - 1] = pm;
+          else tmp[nb_ + nleft + offr + (t - incl)] = pm;
+        }
+        offl += totl;
+        offr += cnt - totl;
+        __syncthreads();
+      }
+      for (uint32_t i = nb_ + t; i < ne_; i += kTB) perm[i] = tmp[i];
+      __syncthreads();
+      if (t == 0) {
+        int c0 = s_count;
+        if ((uint32_t)(c0 + 2) > cap) {
+          raise_error(st, VR_ERR_UNSUPPORTED, 3);
+          nd->axis = -1;
+        } else {
+          CellNode *L = &nodes[base + c0], *R = &nodes[base + c0 + 1];
+          for (int k = 0; k < 3; ++k) {
+            L->lo[k] = R->lo[k] = nd->lo[k];
+            L->hi[k] = R->hi[k] = nd->hi[k];
+          }
+          L->hi[a] = xs;
+          R->lo[a] = xs;
+          L->beg = nb_;
+          L->end = nb_ + nleft;
+          R->beg = nb_ + nleft;
+          R->end = ne_;
+          L->axis = R->axis = -1;
+          nd->axis = a;
+          nd->split = xs;
+          nd->left = c0;
+          nd->right = c0 + 1;
+          s_count = c0 + 2;
+        }
+      }
+      split_done = true;
+      __syncthreads();
+    }
+    if (!split_done && t == 0) nd->axis = -1;
+    __syncthreads();
+  }
+  // leaves: FP64 moments and membership
+  int nleaves = 0;
+  const int count = s_count;
+  for (int cur = 0; cur < count; ++cur) {
+    const CellNode *nd = &nodes[base + cur];
+    if (nd->axis >= 0) continue;
+    ++nleaves;
+    const uint32_t b = nd->beg, e = nd->end;
+    const double M = (double)(e - b);
+    long long sx[3] = {0, 0, 0};
+    double sv[3] = {0, 0, 0};
+    for (uint32_t i = b + t; i < e; i += kTB) {
+      uint32_t m = perm[i];
+      leaf_of[m] = base + cur;
+      int4 p = u[m];
+      float4 q = v[m];
+      sx[0] += p.x; sx[1] += p.y; sx[2] += p.z;
+      sv[0] += (double)q.x; sv[1] += (double)q.y; sv[2] += (double)q.z;
+    }
+    double xm[3], vm[3];
+    for (int k = 0; k < 3; ++k) {
+      xm[k] = (double)block_reduce(sx[k], AddL(), s_rl) / M;
+      vm[k] = block_reduce(sv[k], AddD(), s_rd) / M;
+    }
+    double c[6] = {0, 0, 0, 0, 0, 0};
+    for (uint32_t i = b + t; i < e; i += kTB) {
+      float4 q = v[perm[i]];
+      double d0 = (double)q.x - vm[0], d1 = (double)q.y - vm[1], d2 = (double)q.z - vm[2];
+      c[0] += d0 * d0; c[1] += d1 * d1; c[2] += d2 * d2;
+      c[3] += d0 * d1; c[4] += d0 * d2; c[5] += d1 * d2;
+    }
+    double S6[6];
+    for (int k = 0; k < 6; ++k) S6[k] = block_reduce(c[k], AddD(), s_rd) / M;
+    if (t == 0) {
+      double *o = mom + 13 * (int64_t)(base + cur);
+      o[0] = M;
+      for (int k = 0; k < 3; ++k) { o[1 + k] = xm[k]; o[4 + k] = vm[k]; }
+      for (int k = 0; k < 6; ++k) o[7 + k] = S6[k];
+    }
+  }
+  if (t == 0) hs_out[h * VR_HALO_COLS + VR_H_NCELLS] = (double)nleaves;
+}
+
+// Leaf containing point p, or -1 outside the root region.
+__device__ __forceinline__ int locate(const CellNode *__restrict__ nodes, uint32_t base, const int *p) {
+  const CellNode &r = nodes[base];
+  for (int a = 0; a < 3; ++a)
+    if (p[a] < r.lo[a] || p[a] >= r.hi[a]) return -1;
+  uint32_t id = base;
+  for (int guard = 0; guard < 4096; ++guard) {
+    const CellNode &nd = nodes[id];
+    if (nd.axis < 0) return (int)id;
+    id = base + (p[nd.axis] < nd.split ? nd.left : nd.right);
+  }
+  return -1;
+}
+
+// Cholesky of (xx, yy, zz, xy, xz, yz); false if not positive definite.
+__device__ __forceinline__ bool chol3(const double *s, double *L) {
+  double a00 = s[0], a11 = s[1], a22 = s[2], a10 = s[3], a20 = s[4], a21 = s[5];
+  if (!(a00 > 0.0)) return false;
+  double l00 = sqrt(a00);
+  double l10 = a10 / l00, l20 = a20 / l00;
+  double d1 = a11 - l10 * l10;
+  if (!(d1 > 0.0)) return false;
+  double l11 = sqrt(d1);
+  double l21 = (a21 - l20 * l10) / l11;
+  double d2 = a22 - l20 * l20 - l21 * l21;
+  if (!(d2 > 0.0)) return false;
+  double l22 = sqrt(d2);
+  L[0] = l00; L[1] = l10; L[2] = l11; L[3] = l20; L[4] = l21; L[5] = l22;
+  return true;
+}
+
+__global__ void k_ratio(const uint32_t *__restrict__ hid, const uint32_t *__restrict__ nodeoff,
+                        int64_t nhp, const int4 *__restrict__ u, const float4 *__restrict__ v,
+                        const float *__restrict__ f_l, const CellNode *__restrict__ nodes,
+                        const double *__restrict__ mom, const uint32_t *__restrict__ leaf_of,
+                        float *__restrict__ R, unsigned long long *__restrict__ ndegen) {
+  int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= nhp) return;
+  const uint32_t h = hid[m];
+  const uint32_t base = nodeoff[h];
+  if (nodeoff[h + 1] == base) return;  // halo not searched
+  const int4 p = u[m];
+  const float4 q = v[m];
+  const uint32_t own = leaf_of[m];
+  const CellNode &nd = nodes[own];
+  int cells[7];
+  int nc = 0;
+  cells[nc++] = (int)own;
+  for (int a = 0; a < 3; ++a) {
+    for (int side = 0; side < 2; ++side) {
+      int pp[3] = {p.x, p.y, p.z};
+      pp[a] = side == 0 ? nd.lo[a] - 1 : nd.hi[a];
+      int c = locate(nodes, base, pp);
+      if (c < 0) continue;
+      bool dup = false;
+      for (int k = 0; k < nc; ++k) dup |= cells[k] == c;
+      if (!dup) cells[nc++] = c;
+    }
+  }
+  double w[7];
+  int zero = -1;
+  for (int k = 0; k < nc; ++k) {
+    const double *c = mom + 13 * (int64_t)cells[k];
+    double dx = (double)p.x - c[1], dy = (double)p.y - c[2], dz = (double)p.z - c[3];
+    double r = sqrt(dx * dx + dy * dy + dz * dz);
+    if (r == 0.0) {
+      zero = k;
+      break;
+    }
+    w[k] = 1.0 / r;
+  }
+  double vb[3] = {0, 0, 0}, sg[6] = {0, 0, 0, 0, 0, 0};
+  if (zero >= 0) {
+    const double *c = mom + 13 * (int64_t)cells[zero];
+    for (int k = 0; k < 3; ++k) vb[k] = c[4 + k];
+    for (int k = 0; k < 6; ++k) sg[k] = c[7 + k];
+  } else {
+    double ws = 0.0;
+    for (int k = 0; k < nc; ++k) ws += w[k];
+    for (int k = 0; k < nc; ++k) {
+      const double *c = mom + 13 * (int64_t)cells[k];
+      double f = w[k] / ws;
+      for (int j = 0; j < 3; ++j) vb[j] += f * c[4 + j];
+      for (int j = 0; j < 6; ++j) sg[j] += f * c[7 + j];
+    }
+  }
+  double L[6];
+  const int pidx = __float_as_int(q.w);
+  if (!chol3(sg, L)) {
+    R[pidx] = NAN;
+    atomicAdd(ndegen, 1ULL);
+    return;
+  }
+  double d0 = (double)q.x - vb[0], d1 = (double)q.y - vb[1], d2 = (double)q.z - vb[2];
+  double y0 = d0 / L[0];
+  double y1 = (d1 - L[1] * y0) / L[2];
+  double y2 = (d2 - L[3] * y0 - L[4] * y1) / L[5];
+  double qf = y0 * y0 + y1 * y1 + y2 * y2;
+  const double ln2pi = 1.8378770664093453;  // ln(2 pi)
+  double lnfbg = -0.5 * qf - 1.5 * ln2pi - (log(L[0]) + log(L[2]) + log(L[5]));
+  R[pidx] = (float)(log((double)f_l[pidx]) - lnfbg);
+}
+
+size_t background_bytes(int64_t n, const vr_params *p) {
+  Arena ar;
+  int64_t hmax = n / (p->nmin > 0 ? p->nmin : 1) + 2;
+  ar.take<uint32_t>(hmax + 1);                       // nodeoff
+  ar.take<uint32_t>(n);                              // perm
+  ar.take<uint32_t>(n);                              // tmp
+  ar.take<uint32_t>(n);                              // leaf_of
+  int64_t nodes = max_nodes(n, p);
+  ar.take<CellNode>(nodes);
+  ar.take<double>(13 * nodes);
+  ar.take<char>(scan_scratch_bytes<uint32_t>(hmax + 1));
+  return ar.off;
+}
+
+int64_t max_nodes(int64_t n, const vr_params *p) {
+  // smallest N_cell over searched halos is that of the smallest searched halo
+  int64_t ns = p->nsearch_min;
+  int64_t nc = (int64_t)floor(p->f_cell * (double)ns);
+  if (nc < p->ncell_min) {
+    nc = p->ncell_min;
+    if (ns / 8 < nc) nc = ns / 8;
+  }
+  if (nc < 1) nc = 1;
+  return kNodeFactor * ((n + nc) / (nc + 1)) + 16 * (n / ns + 1) + 16;
+}
+
+vr_status run_background(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Arena &ar,
+                         const float *f_l, float *R, double *halo_stats, Background *out,
+                         cudaStream_t s) {
+  const int64_t H = g.H;
+  int64_t hmax = g.n / (p->nmin > 0 ? p->nmin : 1) + 2;
+  Background &bg = *out;
+  bg.nodeoff = ar.take<uint32_t>(hmax + 1);
+  uint32_t *perm = ar.take<uint32_t>(g.n);
+  uint32_t *tmp = ar.take<uint32_t>(g.n);
+  bg.leaf_of = ar.take<uint32_t>(g.n);
+  int64_t cap = max_nodes(g.n, p);
+  bg.nodes = ar.take<CellNode>(cap);
+  bg.mom = ar.take<double>(13 * cap);
+  void *scr = ar.take<char>(scan_scratch_bytes<uint32_t>(hmax + 1));
+  if (!ar.ok()) return set_error(ctx, VR_ERR_WORKSPACE_TOO_SMALL, "workspace too small");
+  if (H == 0) return VR_OK;
+  VR_TIMED(ctx, "halo_frame", s, k_halo_frame<<<(unsigned)H, kTB, 0, s>>>(g.hoff, g.hlabel, H, g.v, p->nsearch_min, halo_stats));
+  VR_LAUNCHED(ctx, "k_halo_frame");
+  k_node_caps<<<grid_for(H + 1, 256), 256, 0, s>>>(g.hoff, H, p->nsearch_min, p->f_cell,
+                                                   p->ncell_min, bg.nodeoff);
+  VR_LAUNCHED(ctx, "k_node_caps");
+  VR_CUDA(ctx, exclusive_scan<uint32_t>(bg.nodeoff, bg.nodeoff, H + 1, scr, s));
+  VR_TIMED(ctx, "cells_build", s, k_cells_build<<<(unsigned)H, kTB, 0, s>>>(g.hoff, bg.nodeoff, H, g.u, g.v, p->nsearch_min,
+                                           p->f_cell, p->ncell_min, p->split_rule, perm, tmp,
+                                           bg.nodes, bg.mom, bg.leaf_of, halo_stats,
+                                           ctx->d_status));
+  VR_LAUNCHED(ctx, "k_cells_build");
+  unsigned long long *ndeg = (unsigned long long *)&ctx->d_status->info[0];
+  VR_TIMED(ctx, "ratio", s, k_ratio<<<grid_for(g.NHP, 256), 256, 0, s>>>(g.hid, bg.nodeoff, g.NHP, g.u, g.v, f_l, bg.nodes,
+                                               bg.mom, bg.leaf_of, R, ndeg));
+  VR_LAUNCHED(ctx, "k_ratio");
+  return VR_OK;
+}
+
+}  // namespace vr

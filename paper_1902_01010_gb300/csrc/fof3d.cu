@@ -1,0 +1,400 @@
+// 3D friends-of-friends over a periodic lattice box (Sec. 2.1, Eq. fof3d).
+//
+// GB300 design:
+//  1. sub-cells of side S = floor(sqrt((link_d2 - 1) / 3)) + 1, the largest side whose
+//     diagonal is shorter than the linking length: all members of a sub-cell are linked
+//     to each other, so each member is hooked straight below the sub-cell's first
+//     particle without any distance test;
+//  2. link cells of 2 sub-cells per axis (side 2S >= linking length; the last link cell
+//     of each axis takes the 3 or 4 leftover sub-cells, so no link cell is thinner than
+//     the linking length across the periodic edge): every linked pair lies in the same or
+//     an adjacent link cell. Particles are ordered by (Morton code of the link cell,
+//     position of the sub-cell inside it) with the library's radix sort, which makes
+//     every sub-cell, link cell and coarse cell (2^q link cells per axis) one contiguous
+//     run;
+//  3. a dense table over coarse cells gives each link-cell lookup in one load plus a
+//     short binary search;
+//  4. one thread per sub-cell A tests A against the later sub-cells of its own link cell
+//     and all sub-cells of the 13 forward link cells: box distances settle most pairs
+//     (none linked / all linked); the rest are skipped when A and B are already in one
+//     component, otherwise particles are tested until a linked pair is found. Linked
+//     sub-cells are merged by a lock-free union-find (atomicCAS hooks the larger root
+//     under the smaller; finds halve paths);
+//  5. labels are the minimum original index of each component (atomicMin per root).
+// The grid is not a power of two per axis: the last sub-cell of each axis may be
+// partial, and box tests use each cell's true extent across the periodic edge.
+// Positions are gathered once into a 16-byte int4 stream in sorted order.
+#include "vr_internal.cuh"
+#include "vr_workspace.h"
+#include "unionfind.cuh"
+
+namespace vr {
+
+namespace {
+
+constexpr uint32_t kEmpty = 0xffffffffu;
+
+struct FofGeom {
+  int S;        // sub-cell side (lattice units)
+  int G;        // sub-cells per axis (last one partial)
+  int GL;       // link cells per axis: 2 sub-cells each, the last one 3 or 4
+  int bl;       // bits per axis of link-cell coordinates
+  int q;        // coarse cell = 2^q link cells per axis
+  int64_t ncoarse;
+};
+
+// Coarse table size: at most 8^m entries with 8^m <= max(n, 4096), m <= 9 (2^27).
+int coarse_bits_per_axis(int64_t n) {
+  int m = 4;
+  while (m < 9 && (1LL << (3 * (m + 1))) <= n) ++m;
+  return m;
+}
+
+int64_t isqrt64(int64_t x) {
+  int64_t r = (int64_t)sqrt((double)x);
+  while (r * r > x) --r;
+  while ((r + 1) * (r + 1) <= x) ++r;
+  return r;
+}
+
+FofGeom fof_geom(int64_t link_d2, int64_t n) {
+  FofGeom g;
+  g.S = (int)isqrt64((link_d2 - 1) / 3) + 1;  // 3 (S-1)^2 <= link_d2 - 1 < link_d2
+  g.G = (int)((kLattice + g.S - 1) / g.S);
+  g.GL = (g.G - 1) / 2;
+  g.bl = 0;
+  while ((1 << g.bl) < g.GL) ++g.bl;
+  if (g.bl == 0) g.bl = 1;
+  int m = coarse_bits_per_axis(n);
+  g.q = g.bl - m > 0 ? g.bl - m : 0;
+  g.ncoarse = 1LL << (3 * (g.bl - g.q));
+  return g;
+}
+
+struct FofBufs {
+  u64 *k0, *k1;
+  uint32_t *v0, *v1;
+  int4 *posS;
+  int *parent;
+  int *minidx;
+  uint32_t *head;     // 1 at the first particle of each sub-cell, then its exclusive scan
+  uint32_t *sc_start; // first sorted index of each sub-cell
+  uint32_t *cstart, *cend;
+  void *scratch;      // radix sort / scan scratch
+};
+
+FofBufs fof_carve(Arena &ar, int64_t n, int64_t ncoarse) {
+  FofBufs b;
+  b.k0 = ar.take<u64>(n);
+  b.k1 = ar.take<u64>(n);
+  b.v0 = ar.take<uint32_t>(n);
+  b.v1 = ar.take<uint32_t>(n);
+  b.posS = ar.take<int4>(n);
+  b.parent = ar.take<int>(n);
+  b.minidx = ar.take<int>(n);
+  b.head = ar.take<uint32_t>(n + 1);
+  b.sc_start = ar.take<uint32_t>(n + 1);
+  b.cstart = ar.take<uint32_t>(ncoarse);
+  b.cend = ar.take<uint32_t>(ncoarse);
+  size_t a = radix_scratch_bytes<u64>(n), c = scan_scratch_bytes<uint32_t>(n + 1);
+  b.scratch = ar.take<char>(a > c ? a : c);
+  return b;
+}
+
+// Sub-cell c of an axis lies in link cell min(c / 2, GL - 1) at position c - 2 * that.
+__device__ __forceinline__ uint32_t link_of(uint32_t c, int GL) {
+  uint32_t l = c >> 1;
+  return l < (uint32_t)GL ? l : (uint32_t)GL - 1u;
+}
+
+// Sort key: Morton code of the link cell << 6 | 2-bit sub-cell position per axis. Link
+// cells (key >> 6) and coarse cells are its prefixes.
+__global__ void k_fof_keys(const int32_t *__restrict__ pos, int64_t n, int S, int GL,
+                           u64 *__restrict__ keys, uint32_t *__restrict__ vals) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  // masking keeps every cell index in range even for positions outside [0, 2^21)
+  const uint32_t m = (uint32_t)kLattice - 1u;
+  uint32_t x = ((uint32_t)pos[3 * i] & m) / (uint32_t)S,
+           y = ((uint32_t)pos[3 * i + 1] & m) / (uint32_t)S,
+           z = ((uint32_t)pos[3 * i + 2] & m) / (uint32_t)S;
+  uint32_t lx = link_of(x, GL), ly = link_of(y, GL), lz = link_of(z, GL);
+  keys[i] = (morton3(lx, ly, lz) << 6) | ((u64)(x - 2 * lx) << 4) | ((u64)(y - 2 * ly) << 2) |
+            (u64)(z - 2 * lz);
+  vals[i] = (uint32_t)i;
+}
+
+// Sub-cell coordinates of a sort key.
+__device__ __forceinline__ void subcell_of(u64 key, uint32_t *c);
+
+__global__ void k_fof_prepare(const int32_t *__restrict__ pos, const u64 *__restrict__ keyS,
+                              const uint32_t *__restrict__ orig, int64_t n, int cshift,
+                              int4 *__restrict__ posS, int *__restrict__ minidx,
+                              uint32_t *__restrict__ head, uint32_t *__restrict__ cstart,
+                              uint32_t *__restrict__ cend) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p > n) return;
+  if (p == n) {
+    head[n] = 0;
+    return;
+  }
+  int64_t i = orig[p];
+  const uint32_t m = (uint32_t)kLattice - 1u;
+  posS[p] = make_int4((int)((uint32_t)pos[3 * i] & m), (int)((uint32_t)pos[3 * i + 1] & m),
+                      (int)((uint32_t)pos[3 * i + 2] & m), (int)i);
+  minidx[p] = 0x7fffffff;
+  u64 k = keyS[p];
+  head[p] = (p == 0 || keyS[p - 1] != k) ? 1u : 0u;
+  u64 c = k >> cshift;
+  if (p == 0 || (keyS[p - 1] >> cshift) != c) cstart[c] = (uint32_t)p;
+  if (p == n - 1 || (keyS[p + 1] >> cshift) != c) cend[c] = (uint32_t)(p + 1);
+}
+
+// excl[p] = number of sub-cell starts before p (exclusive scan of the start flags).
+// Writes the sub-cell id of every sorted particle and the start of every sub-cell
+// (sc_start[nsc] = n).
+__global__ void k_fof_subcells(const u64 *__restrict__ keyS, const uint32_t *__restrict__ excl,
+                               int64_t n, uint32_t *__restrict__ sid,
+                               uint32_t *__restrict__ sc_start) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  bool first = (p == 0 || keyS[p - 1] != keyS[p]);
+  uint32_t id = excl[p] - (first ? 0u : 1u);
+  sid[p] = id;
+  if (first) sc_start[id] = (uint32_t)p;
+  if (p == n - 1) sc_start[id + 1] = (uint32_t)n;
+}
+
+// Every member of a sub-cell is hooked directly below the sub-cell's first particle:
+// all members are within the linking length of each other (3 (S-1)^2 < link_d2).
+__global__ void k_fof_hook(const uint32_t *__restrict__ sid, const uint32_t *__restrict__ sc_start,
+                           int64_t n, int *__restrict__ parent) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  parent[p] = (int)sc_start[sid[p]];
+}
+
+__device__ __forceinline__ long long d2_periodic(int4 a, int4 b) {
+  long long dx = min_image(a.x - b.x), dy = min_image(a.y - b.y), dz = min_image(a.z - b.z);
+  return dx * dx + dy * dy + dz * dz;
+}
+
+// Forward half of the 26-neighbourhood: (dz > 0) or (dz == 0 and dy > 0) or
+// (dz == 0, dy == 0, dx > 0). With >= 3 link cells per axis each unordered pair of
+// adjacent cells is visited from exactly one side.
+__constant__ signed char c_fwd[13][3] = {
+    {1, 0, 0},  {-1, 1, 0}, {0, 1, 0},  {1, 1, 0},  {-1, -1, 1}, {0, -1, 1}, {1, -1, 1},
+    {-1, 0, 1}, {0, 0, 1},  {1, 0, 1},  {-1, 1, 1}, {0, 1, 1},   {1, 1, 1}};
+
+// Sub-cell extent along one axis: [c S, min((c + 1) S, 2^21) - 1].
+__device__ __forceinline__ void cell_span(int c, int S, int &lo, int &hi) {
+  lo = c * S;
+  hi = min(lo + S, (int)kLattice) - 1;
+}
+
+// Gap and farthest separation between interval A = [alo, ahi] and interval B = [blo, bhi]
+// taken in B's periodic image nearest to A. Returns B's shift into A's frame.
+__device__ __forceinline__ int axis_gap(int alo, int ahi, int blo, int bhi, long long &gap,
+                                        long long &far) {
+  int shift = min_image(blo - alo) - (blo - alo);
+  int b0 = blo + shift, b1 = bhi + shift;
+  long long g = 0;
+  if (b0 > ahi) g = (long long)b0 - ahi;
+  else if (alo > b1) g = (long long)alo - b1;
+  long long f1 = (long long)b1 - alo, f2 = (long long)ahi - b0;
+  gap = g;
+  far = f1 > f2 ? f1 : f2;
+  return shift;
+}
+
+__device__ __forceinline__ uint32_t compact3(u64 x) {
+  x &= 0x1249249249249249ULL;
+  x = (x ^ (x >> 2)) & 0x10c30c30c30c30c3ULL;
+  x = (x ^ (x >> 4)) & 0x100f00f00f00f00fULL;
+  x = (x ^ (x >> 8)) & 0x1f0000ff0000ffULL;
+  x = (x ^ (x >> 16)) & 0x1f00000000ffffULL;
+  x = (x ^ (x >> 32)) & 0x1fffffULL;
+  return (uint32_t)x;
+}
+
+__device__ __forceinline__ void subcell_of(u64 key, uint32_t *c) {
+  const u64 l = key >> 6;
+  c[0] = 2u * compact3(l) + (uint32_t)((key >> 4) & 3u);
+  c[1] = 2u * compact3(l >> 1) + (uint32_t)((key >> 2) & 3u);
+  c[2] = 2u * compact3(l >> 2) + (uint32_t)(key & 3u);
+}
+
+// Links sub-cell A = [a0, a1) with sub-cell B = [b0, b1) if any pair of their members is
+// within the linking length.
+__device__ __forceinline__ void link_subcells(const int4 *__restrict__ posS, int *parent,
+                                              uint32_t a0, uint32_t a1, const int *alo,
+                                              const int *ahi, uint32_t b0, uint32_t b1,
+                                              u64 bkey, int S, long long T) {
+  uint32_t bc[3];
+  subcell_of(bkey, bc);
+  long long mind = 0, maxd = 0;
+  int bl[3], bh[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    int lo, hi;
+    cell_span((int)bc[k], S, lo, hi);
+    long long gp, fr;
+    int sh = axis_gap(alo[k], ahi[k], lo, hi, gp, fr);
+    bl[k] = lo + sh;
+    bh[k] = hi + sh;
+    mind += gp * gp;
+    maxd += fr * fr;
+  }
+  if (mind >= T) return;  // no pair can link
+  if (maxd < T) {         // every pair links
+    uf_unite(parent, (int)a0, (int)b0);
+    return;
+  }
+  if (uf_find(parent, (int)a0) == uf_find(parent, (int)b0)) return;
+  for (uint32_t a = a0; a < a1; ++a) {
+    const int4 xa = posS[a];  // inside A's box, so no wrap in A's frame
+    long long gx = xa.x < bl[0] ? bl[0] - xa.x : (xa.x > bh[0] ? xa.x - bh[0] : 0);
+    long long gy = xa.y < bl[1] ? bl[1] - xa.y : (xa.y > bh[1] ? xa.y - bh[1] : 0);
+    long long gz = xa.z < bl[2] ? bl[2] - xa.z : (xa.z > bh[2] ? xa.z - bh[2] : 0);
+    if (gx * gx + gy * gy + gz * gz >= T) continue;
+    for (uint32_t b = b0; b < b1; ++b) {
+      if (d2_periodic(xa, posS[b]) < T) {
+        uf_unite(parent, (int)a0, (int)b0);
+        return;
+      }
+    }
+  }
+}
+
+// One thread per sub-cell A: A against the later sub-cells of its own link cell and
+// every sub-cell of the 13 forward link cells.
+__global__ void __launch_bounds__(256) k_fof_link(const int4 *__restrict__ posS,
+                                                  const u64 *__restrict__ keyS,
+                                                  const uint32_t *__restrict__ sid,
+                                                  const uint32_t *__restrict__ sc_start,
+                                                  const uint32_t *__restrict__ nsc_ptr,
+                                                  const uint32_t *__restrict__ cstart,
+                                                  const uint32_t *__restrict__ cend, int *parent,
+                                                  int64_t n, int S, int GL, int qshift,
+                                                  long long T) {
+  int64_t A = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (A >= (int64_t)*nsc_ptr) return;
+  const uint32_t a0 = sc_start[A], a1 = sc_start[A + 1];
+  const u64 akey = keyS[a0];
+  int alo[3], ahi[3];
+  uint32_t ac[3];
+  subcell_of(akey, ac);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) cell_span((int)ac[k], S, alo[k], ahi[k]);
+  const u64 lkey = akey >> 6;
+  // later sub-cells of the own link cell
+  for (uint32_t j = a1; j < (uint32_t)n;) {
+    const u64 bk = keyS[j];
+    if ((bk >> 6) != lkey) break;
+    uint32_t j1 = sc_start[sid[j] + 1];
+    link_subcells(posS, parent, a0, a1, alo, ahi, j, j1, bk, S, T);
+    j = j1;
+  }
+  const u64 lk = akey >> 6;
+  const int fx = (int)compact3(lk), fy = (int)compact3(lk >> 1), fz = (int)compact3(lk >> 2);
+#pragma unroll 1
+  for (int s = 0; s < 13; ++s) {
+    int nx = fx + c_fwd[s][0], ny = fy + c_fwd[s][1], nz = fz + c_fwd[s][2];
+    nx = nx < 0 ? nx + GL : (nx >= GL ? nx - GL : nx);
+    ny = ny < 0 ? ny + GL : (ny >= GL ? ny - GL : ny);
+    nz = nz < 0 ? nz + GL : (nz >= GL ? nz - GL : nz);
+    u64 key = morton3((uint32_t)nx, (uint32_t)ny, (uint32_t)nz);  // link-cell key
+    u64 c = key >> qshift;                                        // its coarse cell
+    uint32_t lo = __ldg(&cstart[c]);
+    if (lo == kEmpty) continue;
+    uint32_t hi = __ldg(&cend[c]);
+    while (lo < hi) {
+      uint32_t mid = (lo + hi) >> 1;
+      if ((keyS[mid] >> 6) < key) lo = mid + 1; else hi = mid;
+    }
+    for (uint32_t j = lo; j < (uint32_t)n;) {
+      const u64 bk = keyS[j];
+      if ((bk >> 6) != key) break;
+      uint32_t j1 = sc_start[sid[j] + 1];
+      link_subcells(posS, parent, a0, a1, alo, ahi, j, j1, bk, S, T);
+      j = j1;
+    }
+  }
+}
+
+__global__ void k_fof_roots(int *parent, const int4 *__restrict__ posS, int64_t n,
+                            int *__restrict__ minidx) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  int r = uf_find(parent, (int)p);
+  parent[p] = r;
+  atomicMin(&minidx[r], posS[p].w);
+}
+
+// A fresh find: parent[p] written by k_fof_roots may since have been overwritten by a
+// concurrent path-halving store with an older ancestor, so it is not read directly.
+__global__ void k_fof_label(int *parent, const int4 *__restrict__ posS,
+                            const int *__restrict__ minidx, int64_t n, int32_t *__restrict__ label) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  label[posS[p].w] = minidx[uf_find(parent, (int)p)];
+}
+
+}  // namespace
+
+size_t ws_fof3d(int64_t n) {
+  Arena ar;
+  fof_carve(ar, n, 1LL << (3 * coarse_bits_per_axis(n)));
+  return ar.off;
+}
+
+}  // namespace vr
+
+using namespace vr;
+
+extern "C" vr_status vr_fof3d(vr_ctx *ctx, const int32_t *pos, int64_t n, int64_t link_d2,
+                              int32_t *label, void *ws, size_t ws_bytes, void *stream) {
+  if (!ctx) return VR_ERR_INVALID_ARG;
+  if (n < 0 || n >= (1LL << 31))
+    return set_error(ctx, VR_ERR_INVALID_ARG, "n must be in [0, 2^31)");
+  if (n == 0) return VR_OK;
+  if (!pos || !label || !ws) return set_error(ctx, VR_ERR_INVALID_ARG, "NULL pointer");
+  if (link_d2 < 1 || link_d2 > (1LL << 38))
+    return set_error(ctx, VR_ERR_INVALID_ARG, "link_d2 must be in [1, 2^38]");
+  cudaStream_t s = (cudaStream_t)stream;
+  FofGeom g = fof_geom(link_d2, n);
+  Arena ar(ws, ws_bytes);
+  FofBufs B = fof_carve(ar, n, g.ncoarse);
+  vr_status st = check_ws(ctx, ar, ws_bytes);
+  if (st != VR_OK) return st;
+  const int T = 256;
+  k_fof_keys<<<grid_for(n, T), T, 0, s>>>(pos, n, g.S, g.GL, B.k0, B.v0);
+  VR_LAUNCHED(ctx, "k_fof_keys");
+  int which = 0;
+  VR_CUDA(ctx, radix_sort_pairs<u64>(B.k0, B.v0, B.k1, B.v1, n, 0, 6 + 3 * g.bl, B.scratch, s,
+                                     &which));
+  u64 *keyS = which ? B.k1 : B.k0;
+  uint32_t *orig = which ? B.v1 : B.v0;
+  VR_CUDA(ctx, cudaMemsetAsync(B.cstart, 0xff, g.ncoarse * sizeof(uint32_t), s));
+  const int qshift = 3 * g.q;      // link-cell key -> coarse-cell key
+  const int cshift = 6 + qshift;   // sort key -> coarse-cell key
+  k_fof_prepare<<<grid_for(n + 1, T), T, 0, s>>>(pos, keyS, orig, n, cshift, B.posS, B.minidx,
+                                                 B.head, B.cstart, B.cend);
+  VR_LAUNCHED(ctx, "k_fof_prepare");
+  VR_CUDA(ctx, exclusive_scan<uint32_t>(B.head, B.head, n + 1, B.scratch, s));
+  uint32_t *sid = which ? B.v0 : B.v1;  // the sort's spare value buffer
+  k_fof_subcells<<<grid_for(n, T), T, 0, s>>>(keyS, B.head, n, sid, B.sc_start);
+  VR_LAUNCHED(ctx, "k_fof_subcells");
+  k_fof_hook<<<grid_for(n, T), T, 0, s>>>(sid, B.sc_start, n, B.parent);
+  VR_LAUNCHED(ctx, "k_fof_hook");
+  // the number of sub-cells, head[n], stays on the device; threads beyond it idle
+  VR_TIMED(ctx, "fof_link", s, k_fof_link<<<grid_for(n, T), T, 0, s>>>(B.posS, keyS, sid, B.sc_start, B.head + n, B.cstart,
+                                          B.cend, B.parent, n, g.S, g.GL, qshift,
+                                          (long long)link_d2));
+  VR_LAUNCHED(ctx, "k_fof_link");
+  k_fof_roots<<<grid_for(n, T), T, 0, s>>>(B.parent, B.posS, n, B.minidx);
+  VR_LAUNCHED(ctx, "k_fof_roots");
+  k_fof_label<<<grid_for(n, T), T, 0, s>>>(B.parent, B.posS, B.minidx, n, label);
+  VR_LAUNCHED(ctx, "k_fof_label");
+  return VR_OK;
+}

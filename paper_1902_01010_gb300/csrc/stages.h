@@ -1,0 +1,18 @@
+// Stage entry points shared between the substructure translation units.
+#pragma once
+#include "halos.cuh"
+#include "background.cuh"
+
+namespace vr {
+size_t velden_bytes(int64_t n, int nmin);
+vr_status run_velden(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Arena &ar, float *f_l,
+                     cudaStream_t s);
+vr_status fill_f32(vr_ctx *ctx, float *a, int64_t n, float val, cudaStream_t s);
+vr_status fill_i32(vr_ctx *ctx, int32_t *a, int64_t n, int32_t val, cudaStream_t s);
+vr_status run_fit(vr_ctx *ctx, const HaloSeg &g, const Background &bg, const vr_params *p,
+                  const float *R, double *halo_stats, float *ell, cudaStream_t s);
+size_t fof6d_bytes(int64_t n, int nmin);
+vr_status run_fof6d(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Arena &ar,
+                    const float *ell, const double *hp, int64_t nhalo, int32_t *label6,
+                    cudaStream_t s);
+}  // namespace vr

@@ -1,0 +1,146 @@
+// C-ABI entry points of the substructure stages (Sec. 2.2): argument checks, workspace
+// carving and stage sequencing. The kernels live in halos.cu, velden.cu, background.cu,
+// ellfit.cu and fof6d.cu.
+#include <math.h>
+
+#include "stages.h"
+#include "vr_workspace.h"
+
+namespace vr {
+
+size_t ws_substructure(int64_t n, const vr_params *p) {
+  size_t a = velden_bytes(n, p->nmin), b = background_bytes(n, p), c = fof6d_bytes(n, p->nmin);
+  size_t m = a > b ? a : b;
+  m = m > c ? m : c;
+  return halo_seg_bytes(n, p->nmin) + m + 4096;
+}
+
+namespace {
+
+vr_status common_checks(vr_ctx *ctx, int64_t n, const vr_params *p) {
+  if (n < 0 || n >= (1LL << 31)) return set_error(ctx, VR_ERR_INVALID_ARG, "n must be in [0, 2^31)");
+  return params_check(ctx, p);
+}
+
+// Per-halo linking lengths of the substructure search: lx2 = lx_sub^2 for every
+// searched halo, lv2 = (alpha_lv sigma_host)^2.
+__global__ void k_link_lengths(double *hs, int64_t H, double lx_sub, double alpha_lv) {
+  int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= H) return;
+  double *row = hs + h * VR_HALO_COLS;
+  if (row[VR_H_SEARCHED] == 0.0) return;
+  row[VR_H_LX2] = __dmul_rn(lx_sub, lx_sub);
+  double t = __dmul_rn(alpha_lv, row[VR_H_SIGMA]);
+  row[VR_H_LV2] = __dmul_rn(t, t);
+}
+
+}  // namespace
+}  // namespace vr
+
+using namespace vr;
+
+extern "C" {
+
+vr_status vr_velden(vr_ctx *ctx, const int32_t *pos, const float *vel, int64_t n,
+                    const int32_t *label, const vr_params *p, float *f_l, void *ws,
+                    size_t ws_bytes, void *stream) {
+  if (!ctx) return VR_ERR_INVALID_ARG;
+  vr_status st = common_checks(ctx, n, p);
+  if (st != VR_OK) return st;
+  if (n == 0) return VR_OK;
+  if (!pos || !vel || !label || !f_l || !ws) return set_error(ctx, VR_ERR_INVALID_ARG, "NULL pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  Arena ar(ws, ws_bytes);
+  HaloSeg g;
+  st = fill_f32(ctx, f_l, n, NAN, s);
+  if (st != VR_OK) return st;
+  st = build_halos(ctx, pos, vel, n, label, p->nmin, p->nse, ar, s, &g);
+  if (st != VR_OK) return st;
+  return run_velden(ctx, g, p, ar, f_l, s);
+}
+
+vr_status vr_outlier_ratio(vr_ctx *ctx, const int32_t *pos, const float *vel, const float *f_l,
+                           int64_t n, const int32_t *label, const vr_params *p, float *R,
+                           float *ell, double *halo_stats, int64_t *nhalo, void *ws,
+                           size_t ws_bytes, void *stream) {
+  if (!ctx) return VR_ERR_INVALID_ARG;
+  vr_status st = common_checks(ctx, n, p);
+  if (st != VR_OK) return st;
+  if (nhalo) *nhalo = 0;
+  if (n == 0) return VR_OK;
+  if (!pos || !vel || !f_l || !label || !R || !ell || !halo_stats || !ws)
+    return set_error(ctx, VR_ERR_INVALID_ARG, "NULL pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  Arena ar(ws, ws_bytes);
+  HaloSeg g;
+  if ((st = fill_f32(ctx, R, n, NAN, s)) != VR_OK) return st;
+  if ((st = fill_f32(ctx, ell, n, NAN, s)) != VR_OK) return st;
+  if ((st = build_halos(ctx, pos, vel, n, label, p->nmin, p->nse, ar, s, &g)) != VR_OK) return st;
+  Background bg;
+  if ((st = run_background(ctx, g, p, ar, f_l, R, halo_stats, &bg, s)) != VR_OK) return st;
+  if ((st = run_fit(ctx, g, bg, p, R, halo_stats, ell, s)) != VR_OK) return st;
+  if (nhalo) *nhalo = g.H;
+  return read_status(ctx, s, nullptr);
+}
+
+vr_status vr_fof6d(vr_ctx *ctx, const int32_t *pos, const float *vel, const float *ell,
+                   int64_t n, const int32_t *label, const double *halo_params, int64_t nhalo,
+                   const vr_params *p, int32_t *label6, void *ws, size_t ws_bytes,
+                   void *stream) {
+  if (!ctx) return VR_ERR_INVALID_ARG;
+  vr_status st = common_checks(ctx, n, p);
+  if (st != VR_OK) return st;
+  if (n == 0) return VR_OK;
+  if (!pos || !vel || !label || !halo_params || !label6 || !ws)
+    return set_error(ctx, VR_ERR_INVALID_ARG, "NULL pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  Arena ar(ws, ws_bytes);
+  HaloSeg g;
+  if ((st = fill_i32(ctx, label6, n, -1, s)) != VR_OK) return st;
+  if ((st = build_halos(ctx, pos, vel, n, label, p->nmin, p->nse, ar, s, &g)) != VR_OK) return st;
+  if (nhalo != g.H)
+    return set_error(ctx, VR_ERR_INVALID_ARG, "nhalo = %lld but the labels define %lld halos",
+                     (long long)nhalo, (long long)g.H);
+  return run_fof6d(ctx, g, p, ar, ell, halo_params, nhalo, label6, s);
+}
+
+vr_status vr_find_substructure(vr_ctx *ctx, const int32_t *pos, const float *vel, int64_t n,
+                               const int32_t *label, double lx_sub, double alpha_lv,
+                               const vr_params *p, int batched, float *f_l, float *R,
+                               float *ell, int32_t *label6, double *halo_stats, int64_t *nhalo,
+                               void *ws, size_t ws_bytes, void *stream) {
+  if (!ctx) return VR_ERR_INVALID_ARG;
+  vr_status st = common_checks(ctx, n, p);
+  if (st != VR_OK) return st;
+  if (nhalo) *nhalo = 0;
+  if (n == 0) return VR_OK;
+  if (!pos || !vel || !label || !f_l || !R || !ell || !label6 || !halo_stats || !ws)
+    return set_error(ctx, VR_ERR_INVALID_ARG, "NULL pointer");
+  if (!(lx_sub > 0.0) || !(alpha_lv > 0.0))
+    return set_error(ctx, VR_ERR_INVALID_ARG, "lx_sub and alpha_lv must be positive");
+  (void)batched;
+  cudaStream_t s = (cudaStream_t)stream;
+  Arena ar(ws, ws_bytes);
+  HaloSeg g;
+  if ((st = fill_f32(ctx, f_l, n, NAN, s)) != VR_OK) return st;
+  if ((st = fill_f32(ctx, R, n, NAN, s)) != VR_OK) return st;
+  if ((st = fill_f32(ctx, ell, n, NAN, s)) != VR_OK) return st;
+  if ((st = fill_i32(ctx, label6, n, -1, s)) != VR_OK) return st;
+  if ((st = build_halos(ctx, pos, vel, n, label, p->nmin, p->nse, ar, s, &g)) != VR_OK) return st;
+  const size_t mark = ar.off;
+  if ((st = run_velden(ctx, g, p, ar, f_l, s)) != VR_OK) return st;
+  ar.off = mark;
+  Background bg;
+  if ((st = run_background(ctx, g, p, ar, f_l, R, halo_stats, &bg, s)) != VR_OK) return st;
+  if ((st = run_fit(ctx, g, bg, p, R, halo_stats, ell, s)) != VR_OK) return st;
+  ar.off = mark;
+  if (g.H > 0) {
+    k_link_lengths<<<grid_for(g.H, 256), 256, 0, s>>>(halo_stats, g.H, lx_sub, alpha_lv);
+    VR_LAUNCHED(ctx, "k_link_lengths");
+  }
+  if ((st = run_fof6d(ctx, g, p, ar, ell, halo_stats, g.H, label6, s)) != VR_OK) return st;
+  if (nhalo) *nhalo = g.H;
+  return read_status(ctx, s, nullptr);
+}
+
+}  // extern "C"

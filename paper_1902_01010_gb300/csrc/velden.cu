@@ -1,0 +1,494 @@
+// Local velocity density f_l (Sec. 2.2): Epanechnikov estimate from the N_v nearest in
+// velocity among the N_se nearest in position, inside each halo.
+//
+// GB300 design (no neighbour list is ever materialised):
+//  - halo members are Morton-ordered inside their halo (halos.cu); each run of 32
+//    consecutive members is a "bucket" with an integer bounding box, and 32 consecutive
+//    buckets of one halo form a "super-bucket";
+//  - one warp handles one bucket: lane k is the query particle k. An upper bound R_k on
+//    the N_se-th neighbour distance comes from the N_se members around the bucket in
+//    Morton order; every pass then visits the buckets whose boxes come within the
+//    largest per-lane bound of the warp's own box (super-bucket boxes prune first), and
+//    each pass tightens the per-lane bounds;
+//  - the candidates stream through the warp 32 at a time (one coalesced int4 load, then
+//    register shuffles), and every lane keeps its own 64-bin histogram of the exact key
+//    (d^2 << 22 | local index) in shared memory. Histogram passes narrow the key range
+//    until the bin holding the N_se-th key has at most 32 keys; a last pass feeds every
+//    key below that bin, plus the right number from the bin, into a per-lane list of the
+//    N_v smallest |dv|^2 (shared memory);
+//  - h^2 is the largest kept |dv|^2, and the kernel sum runs over the kept list only
+//    (every neighbour with |dv| < h is in it).
+// Position keys are exact integers, so the N_se set equals the oracle's; velocities
+// differences and sums are FP32.
+// Halos with at most N_se members use every member (one pass, no position search).
+#include <math.h>
+
+#include "halos.cuh"
+#include "vr_workspace.h"
+
+namespace vr {
+
+namespace {
+
+constexpr int kNVMax = 64;
+constexpr int kBins = 64;
+constexpr int kBuf = 32;
+constexpr int kWarps = 4;        // warps per block
+
+struct WarpSmem {
+  uint16_t hist[kBins][32];
+  u64 bkey[kBuf][32];
+  float bdv[kBuf][32];
+  float top[kNVMax][32];
+};
+
+struct SmallSmem {
+  float top[kNVMax][32];
+};
+
+// Per-lane list of the nv smallest values (unsorted) with its current maximum.
+struct TopV {
+  int c, im;
+  float m;
+};
+
+__device__ __forceinline__ void top_insert(float (*top)[32], int lane, TopV &t, int nv, float v) {
+  if (t.c < nv) {
+    top[t.c][lane] = v;
+    if (t.c == 0 || v > t.m) {
+      t.m = v;
+      t.im = t.c;
+    }
+    t.c++;
+  } else if (v < t.m) {
+    top[t.im][lane] = v;
+    float m = top[0][lane];
+    int im = 0;
+    for (int q = 1; q < nv; ++q) {
+      float x = top[q][lane];
+      if (x > m) {
+        m = x;
+        im = q;
+      }
+    }
+    t.m = m;
+    t.im = im;
+  }
+}
+
+// f_l from the kept list: h^2 = largest kept |dv|^2 (the N_v-th smallest);
+// f_l = 15/(8 pi h^3) * sum_{|dv| < h} (1 - |dv|^2/h^2) / N_se_eff.
+__device__ __forceinline__ float top_density(float (*top)[32], int lane, const TopV &t,
+                                             int nse_eff) {
+  float h2 = t.m;
+  if (!(h2 > 0.0f)) return INFINITY;
+  float inv = 1.0f / h2;
+  float sum = 0.0f;
+  for (int q = 0; q < t.c; ++q) {
+    float x = top[q][lane];
+    if (x < h2) sum += 1.0f - x * inv;
+  }
+  float h = sqrtf(h2);
+  const float c = 15.0f / (8.0f * 3.14159265358979f);
+  return c / (h2 * h) * sum / (float)nse_eff;
+}
+
+__device__ __forceinline__ float dv2f(float4 a, float4 b) {
+  float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+  return dx * dx + dy * dy + dz * dz;
+}
+
+__device__ __forceinline__ long long d2i(int4 a, int4 b) {
+  long long dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+  return dx * dx + dy * dy + dz * dz;
+}
+
+// ---------------------------------------------------------------- small halos
+__global__ void __launch_bounds__(32 * kWarps) k_velden_small(
+    const uint32_t *__restrict__ hoff, const uint32_t *__restrict__ hlabel, int64_t H,
+    const float4 *__restrict__ v, int nse, int nv, float *__restrict__ f_l) {
+  __shared__ SmallSmem sm[kWarps];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int64_t h = (int64_t)blockIdx.x * kWarps + w;
+  if (h >= H) return;
+  const uint32_t hs = hoff[h], he = hoff[h + 1];
+  const int nh = (int)(he - hs);
+  if (nh > nse) return;
+  const int nv_eff = nv < nh ? nv : nh;
+  float(*top)[32] = sm[w].top;
+  for (uint32_t qb = hs; qb < he; qb += 32) {
+    const uint32_t k = qb + lane;
+    const bool valid = k < he;
+    const float4 vq = v[valid ? k : hs];
+    TopV t = {0, 0, 0.0f};
+    for (uint32_t jb = hs; jb < he; jb += 32) {
+      const uint32_t j = jb + lane;
+      const float4 vj = v[j < he ? j : hs];
+      const int cnt = (int)min(32u, he - jb);
+      for (int tt = 0; tt < cnt; ++tt) {
+        float4 vt;
+        vt.x = __shfl_sync(0xffffffffu, vj.x, tt);
+        vt.y = __shfl_sync(0xffffffffu, vj.y, tt);
+        vt.z = __shfl_sync(0xffffffffu, vj.z, tt);
+        if (valid) top_insert(top, lane, t, nv_eff, dv2f(vt, vq));
+      }
+    }
+    if (valid) f_l[__float_as_int(vq.w)] = top_density(top, lane, t, nh);
+  }
+  (void)hlabel;
+}
+
+// ------------------------------------------------------------- bucket boxes
+// Buckets of halo h occupy the padded index range [32 sboff[h], 32 sboff[h+1]); bucket
+// b of the halo holds slots [hoff[h] + 32 b, min(hoff[h+1], hoff[h] + 32 b + 32)).
+__global__ void k_sb_count(const uint32_t *__restrict__ hoff, int64_t H, int nse,
+                           uint32_t *__restrict__ nsb) {
+  int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (h > H) return;
+  if (h == H) {
+    nsb[H] = 0;
+    return;
+  }
+  uint32_t nh = hoff[h + 1] - hoff[h];
+  uint32_t nb = (nh + 31) / 32;
+  nsb[h] = nh > (uint32_t)nse ? (nb + 31) / 32 : 0;
+}
+
+__global__ void k_sb_fill(const uint32_t *__restrict__ sboff, int64_t H, uint32_t *__restrict__ sbhalo) {
+  int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= H) return;
+  for (uint32_t s = sboff[h]; s < sboff[h + 1]; ++s) sbhalo[s] = (uint32_t)h;
+}
+
+__global__ void k_bucket_boxes(const uint32_t *__restrict__ hoff, const uint32_t *__restrict__ sboff,
+                               const uint32_t *__restrict__ sbhalo, int64_t nbpad,
+                               const int4 *__restrict__ u, int4 *__restrict__ bmin,
+                               int4 *__restrict__ bmax) {
+  int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nbpad) return;
+  uint32_t h = sbhalo[b >> 5];
+  uint32_t local = (uint32_t)b - 32u * sboff[h];
+  uint32_t s0 = hoff[h] + 32u * local, s1 = min(s0 + 32u, hoff[h + 1]);
+  int4 lo = make_int4(0x7fffffff, 0x7fffffff, 0x7fffffff, 0);
+  int4 hi = make_int4(-0x7fffffff, -0x7fffffff, -0x7fffffff, 0);
+  for (uint32_t m = s0; m < s1; ++m) {
+    int4 p = u[m];
+    lo.x = min(lo.x, p.x); lo.y = min(lo.y, p.y); lo.z = min(lo.z, p.z);
+    hi.x = max(hi.x, p.x); hi.y = max(hi.y, p.y); hi.z = max(hi.z, p.z);
+  }
+  bmin[b] = lo;  // empty (padding) buckets keep an inverted box
+  bmax[b] = hi;
+}
+
+__global__ void k_superbucket_boxes(int64_t nsb, const int4 *__restrict__ bmin,
+                                    const int4 *__restrict__ bmax, int4 *__restrict__ smin,
+                                    int4 *__restrict__ smax) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nsb) return;
+  int4 lo = make_int4(0x7fffffff, 0x7fffffff, 0x7fffffff, 0);
+  int4 hi = make_int4(-0x7fffffff, -0x7fffffff, -0x7fffffff, 0);
+  for (int k = 0; k < 32; ++k) {
+    int4 a = bmin[32 * s + k], c = bmax[32 * s + k];
+    lo.x = min(lo.x, a.x); lo.y = min(lo.y, a.y); lo.z = min(lo.z, a.z);
+    hi.x = max(hi.x, c.x); hi.y = max(hi.y, c.y); hi.z = max(hi.z, c.z);
+  }
+  smin[s] = lo;
+  smax[s] = hi;
+}
+
+__device__ __forceinline__ long long gap1(int alo, int ahi, int blo, int bhi) {
+  long long g = 0;
+  if (blo > ahi) g = (long long)blo - ahi;
+  else if (alo > bhi) g = (long long)alo - bhi;
+  return g;
+}
+__device__ __forceinline__ long long box_d2(int4 alo, int4 ahi, int4 blo, int4 bhi) {
+  long long gx = gap1(alo.x, ahi.x, blo.x, bhi.x), gy = gap1(alo.y, ahi.y, blo.y, bhi.y),
+            gz = gap1(alo.z, ahi.z, blo.z, bhi.z);
+  return gx * gx + gy * gy + gz * gz;
+}
+__device__ __forceinline__ long long pt_box_d2(int4 p, int4 blo, int4 bhi) {
+  return box_d2(p, p, blo, bhi);
+}
+
+__device__ __forceinline__ int bitlen64(unsigned long long x) { return x ? 64 - __clzll(x) : 0; }
+
+// ---------------------------------------------------------------- big halos
+__global__ void __launch_bounds__(32 * kWarps) k_velden_big(
+    const uint32_t *__restrict__ hoff, const uint32_t *__restrict__ sboff,
+    const uint32_t *__restrict__ sbhalo, int64_t nbpad, const int4 *__restrict__ u,
+    const float4 *__restrict__ v, const int4 *__restrict__ bmin, const int4 *__restrict__ bmax,
+    const int4 *__restrict__ smin, const int4 *__restrict__ smax, int nse, int nv,
+    float *__restrict__ f_l, DevStatus *st) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  WarpSmem &sm = reinterpret_cast<WarpSmem *>(smem_raw)[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
+  const unsigned FULL = 0xffffffffu;
+  const int64_t b = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  if (b >= nbpad) return;
+  const uint32_t h = sbhalo[b >> 5];
+  const uint32_t hs = hoff[h], he = hoff[h + 1];
+  const uint32_t nh = he - hs;
+  const uint32_t local = (uint32_t)b - 32u * sboff[h];
+  const uint32_t nbh = (nh + 31) / 32;
+  if (local >= nbh) return;  // padding bucket
+  const uint32_t qs = hs + 32u * local, qe = min(qs + 32u, he);
+  const uint32_t k = qs + lane;
+  const bool valid = k < qe;
+  const int4 q = u[valid ? k : qs];
+  const float4 vq = v[valid ? k : qs];
+  const int nse_eff = nse;  // nh > nse here
+  const int nv_eff = nv;
+  // 1. bound from the N_se members around the bucket in Morton order
+  long long r2 = 0;
+  {
+    int64_t w0 = (int64_t)qs + 16 - nse / 2;
+    if (w0 + nse > (int64_t)he) w0 = (int64_t)he - nse;
+    if (w0 < (int64_t)hs) w0 = hs;
+    for (int c = 0; c < nse; c += 32) {
+      int64_t j = w0 + c + lane;
+      int4 p = u[j < w0 + nse ? j : w0];
+      int cnt = min(32, nse - c);
+      for (int t = 0; t < cnt; ++t) {
+        int4 pt;
+        pt.x = __shfl_sync(FULL, p.x, t);
+        pt.y = __shfl_sync(FULL, p.y, t);
+        pt.z = __shfl_sync(FULL, p.z, t);
+        long long d = d2i(q, pt);
+        r2 = d > r2 ? d : r2;
+      }
+    }
+  }
+  if (r2 >= (1LL << 41)) {
+    raise_error(st, VR_ERR_UNSUPPORTED, 1);
+    return;
+  }
+  // Candidate buckets are enumerated on the fly in every pass: super-bucket boxes, then
+  // bucket boxes, against the query bucket's box grown by the largest per-lane bound;
+  // f(bucket_slot_start) is called warp-uniformly for every bucket that passes.
+  const int4 qlo = bmin[b], qhi = bmax[b];
+  const uint32_t sb0 = sboff[h], sb1 = sboff[h + 1];
+  auto for_each_bucket = [&](long long rmax2, auto &&f) {
+    for (uint32_t sbase = sb0; sbase < sb1; sbase += 32) {
+      uint32_t sx = sbase + lane;
+      bool hit = sx < sb1 && box_d2(qlo, qhi, smin[sx], smax[sx]) <= rmax2;
+      unsigned hm = __ballot_sync(FULL, hit);
+      while (hm) {
+        int t = __ffs(hm) - 1;
+        hm &= hm - 1;
+        uint32_t bb = 32u * (sbase + t) + lane;
+        bool in = (bb - 32u * sb0) < nbh && box_d2(qlo, qhi, bmin[bb], bmax[bb]) <= rmax2;
+        unsigned bm = __ballot_sync(FULL, in);
+        while (bm) {
+          int tb = __ffs(bm) - 1;
+          bm &= bm - 1;
+          f(32u * (sbase + t) + (uint32_t)tb);
+        }
+      }
+    }
+  };
+  auto warp_max = [&](long long x) {
+    for (int o = 16; o; o >>= 1) {
+      long long y = __shfl_xor_sync(FULL, x, o);
+      x = y > x ? y : x;
+    }
+    return x;
+  };
+  // 2. histogram passes over the exact keys (d^2 << 22 | local index)
+  u64 klo = 0;
+  int sh = bitlen64(((u64)(r2 + 1) << 22) - 1) - 6;
+  if (sh < 0) sh = 0;
+  int need = nse_eff;
+  bool settled = !valid;
+  u64 fin_lo = 0, fin_hi = 0;
+  int need_in = 0;
+  long long rcur = r2;  // per-lane bound on d^2 of keys still of interest
+  for (int level = 0; level < 12; ++level) {
+    if (!settled)
+      for (int c = 0; c < kBins; ++c) sm.hist[c][lane] = 0;
+    const long long rmax2 = warp_max(settled ? 0 : rcur);
+    for_each_bucket(rmax2, [&](uint32_t bb) {
+      bool want = !settled && pt_box_d2(q, bmin[bb], bmax[bb]) <= rcur;
+      if (!__any_sync(FULL, want)) return;
+      const uint32_t s0 = hs + 32u * (bb - 32u * sb0);
+      const int cnt = (int)min(32u, he - s0);
+      const int4 p = u[s0 + (lane < cnt ? lane : 0)];
+      for (int t = 0; t < cnt; ++t) {
+        int4 pt;
+        pt.x = __shfl_sync(FULL, p.x, t);
+        pt.y = __shfl_sync(FULL, p.y, t);
+        pt.z = __shfl_sync(FULL, p.z, t);
+        pt.w = __shfl_sync(FULL, p.w, t);
+        if (want) {
+          long long d = d2i(q, pt);
+          if (d <= rcur) {
+            u64 key = ((u64)d << 22) | (u64)pt.w;
+            if (key >= klo) {
+              u64 rel = (key - klo) >> sh;
+              if (rel < kBins) sm.hist[rel][lane]++;
+            }
+          }
+        }
+      }
+    });
+    if (!settled) {
+      int cum = 0, bs = kBins - 1;
+      for (int c = 0; c < kBins; ++c) {
+        int hc = sm.hist[c][lane];
+        if (cum + hc >= need) {
+          bs = c;
+          break;
+        }
+        cum += hc;
+      }
+      int hc = sm.hist[bs][lane];
+      if (hc <= kBuf || sh == 0) {
+        fin_lo = klo + ((u64)bs << sh);
+        fin_hi = fin_lo + ((u64)1 << sh);
+        need_in = need - cum;
+        settled = true;
+      } else {
+        klo += (u64)bs << sh;
+        need -= cum;
+        const long long top_d = (long long)((klo + ((u64)1 << sh) - 1) >> 22);
+        rcur = top_d < rcur ? top_d : rcur;
+        sh = sh >= 6 ? sh - 6 : 0;
+      }
+    }
+    if (__all_sync(FULL, settled)) break;
+  }
+  // 3. collect: keys below the final bin are in; the final bin is buffered
+  if (valid) {
+    const long long top_d = (long long)((fin_hi - 1) >> 22);
+    rcur = top_d < r2 ? top_d : r2;
+  } else {
+    rcur = -1;
+  }
+  float(*top)[32] = sm.top;
+  TopV tv = {0, 0, 0.0f};
+  int nbuf = 0;
+  for_each_bucket(warp_max(rcur), [&](uint32_t bb) {
+    bool want = valid && pt_box_d2(q, bmin[bb], bmax[bb]) <= rcur;
+    if (!__any_sync(FULL, want)) return;
+    const uint32_t s0 = hs + 32u * (bb - 32u * sb0);
+    const int cnt = (int)min(32u, he - s0);
+    const int4 p = u[s0 + (lane < cnt ? lane : 0)];
+    const float4 pv = v[s0 + (lane < cnt ? lane : 0)];
+    for (int t = 0; t < cnt; ++t) {
+      int4 pt;
+      float4 vt;
+      pt.x = __shfl_sync(FULL, p.x, t);
+      pt.y = __shfl_sync(FULL, p.y, t);
+      pt.z = __shfl_sync(FULL, p.z, t);
+      pt.w = __shfl_sync(FULL, p.w, t);
+      vt.x = __shfl_sync(FULL, pv.x, t);
+      vt.y = __shfl_sync(FULL, pv.y, t);
+      vt.z = __shfl_sync(FULL, pv.z, t);
+      if (want) {
+        long long d = d2i(q, pt);
+        if (d <= rcur) {
+          u64 key = ((u64)d << 22) | (u64)pt.w;
+          if (key < fin_lo) {
+            top_insert(top, lane, tv, nv_eff, dv2f(vt, vq));
+          } else if (key < fin_hi && nbuf < kBuf) {
+            sm.bkey[nbuf][lane] = key;
+            sm.bdv[nbuf][lane] = dv2f(vt, vq);
+            ++nbuf;
+          }
+        }
+      }
+    }
+  });
+  if (!valid) return;
+  // the need_in smallest keys of the final bin
+  for (int r = 0; r < need_in; ++r) {
+    int best = -1;
+    u64 bk = ~0ULL;
+    for (int e = 0; e < nbuf; ++e) {
+      u64 x = sm.bkey[e][lane];
+      if (x < bk) {
+        bk = x;
+        best = e;
+      }
+    }
+    if (best < 0) break;
+    sm.bkey[best][lane] = ~0ULL;
+    top_insert(top, lane, tv, nv_eff, sm.bdv[best][lane]);
+  }
+  f_l[__float_as_int(vq.w)] = top_density(top, lane, tv, nse_eff);
+}
+
+__global__ void k_fill_f32(float *__restrict__ a, int64_t n, float val) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = val;
+}
+
+}  // namespace
+
+size_t velden_bytes(int64_t n, int nmin) {
+  Arena ar;
+  int64_t hmax = n / (nmin > 0 ? nmin : 1) + 2;
+  int64_t nbmax = n / 32 + 32 * hmax + 64;  // padded buckets
+  ar.take<uint32_t>(hmax + 1);  // nsb / sboff
+  ar.take<uint32_t>(nbmax / 32 + 1);  // sbhalo
+  ar.take<int4>(nbmax);   // bmin
+  ar.take<int4>(nbmax);   // bmax
+  ar.take<int4>(nbmax / 32 + 1);  // smin
+  ar.take<int4>(nbmax / 32 + 1);  // smax
+  ar.take<char>(scan_scratch_bytes<uint32_t>(hmax + 1));
+  return ar.off;
+}
+
+// Runs the f_l stage on an existing segmentation; f_l must already hold NaN outside
+// halos.
+vr_status run_velden(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Arena &ar, float *f_l,
+                     cudaStream_t s) {
+  if (g.H == 0) return VR_OK;
+  const int64_t H = g.H;
+  int64_t hmax = g.n / (p->nmin > 0 ? p->nmin : 1) + 2;
+  int64_t nbmax = g.n / 32 + 32 * hmax + 64;
+  uint32_t *sboff = ar.take<uint32_t>(hmax + 1);
+  uint32_t *sbhalo = ar.take<uint32_t>(nbmax / 32 + 1);
+  int4 *bmin = ar.take<int4>(nbmax);
+  int4 *bmax = ar.take<int4>(nbmax);
+  int4 *smin = ar.take<int4>(nbmax / 32 + 1);
+  int4 *smax = ar.take<int4>(nbmax / 32 + 1);
+  void *scr = ar.take<char>(scan_scratch_bytes<uint32_t>(hmax + 1));
+  if (!ar.ok()) return set_error(ctx, VR_ERR_WORKSPACE_TOO_SMALL, "workspace too small");
+  const int T = 256;
+  // small halos: all members are neighbours
+  VR_TIMED(ctx, "velden_small", s, k_velden_small<<<grid_for(H, kWarps), 32 * kWarps, 0, s>>>(g.hoff, g.hlabel, H, g.v, p->nse,
+                                                            p->nv, f_l));
+  VR_LAUNCHED(ctx, "k_velden_small");
+  k_sb_count<<<grid_for(H + 1, T), T, 0, s>>>(g.hoff, H, p->nse, sboff);
+  VR_LAUNCHED(ctx, "k_sb_count");
+  VR_CUDA(ctx, exclusive_scan<uint32_t>(sboff, sboff, H + 1, scr, s));
+  VR_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned + 34, sboff + H, sizeof(uint32_t),
+                               cudaMemcpyDeviceToHost, s));
+  VR_CUDA(ctx, cudaStreamSynchronize(s));
+  uint32_t nsb = 0;
+  memcpy(&nsb, ctx->h_pinned + 34, 4);
+  if (nsb == 0) return VR_OK;
+  int64_t nbpad = 32LL * nsb;
+  k_sb_fill<<<grid_for(H, T), T, 0, s>>>(sboff, H, sbhalo);
+  VR_LAUNCHED(ctx, "k_sb_fill");
+  k_bucket_boxes<<<grid_for(nbpad, T), T, 0, s>>>(g.hoff, sboff, sbhalo, nbpad, g.u, bmin, bmax);
+  VR_LAUNCHED(ctx, "k_bucket_boxes");
+  k_superbucket_boxes<<<grid_for(nsb, T), T, 0, s>>>(nsb, bmin, bmax, smin, smax);
+  VR_LAUNCHED(ctx, "k_superbucket_boxes");
+  size_t shm = sizeof(WarpSmem) * kWarps;
+  VR_CUDA(ctx, cudaFuncSetAttribute(k_velden_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+  VR_TIMED(ctx, "velden_big", s, k_velden_big<<<grid_for(nbpad, kWarps), 32 * kWarps, shm, s>>>(
+      g.hoff, sboff, sbhalo, nbpad, g.u, g.v, bmin, bmax, smin, smax, p->nse, p->nv, f_l,
+      ctx->d_status));
+  VR_LAUNCHED(ctx, "k_velden_big");
+  return VR_OK;
+}
+
+vr_status fill_f32(vr_ctx *ctx, float *a, int64_t n, float val, cudaStream_t s) {
+  k_fill_f32<<<grid_for(n, 256), 256, 0, s>>>(a, n, val);
+  VR_LAUNCHED(ctx, "k_fill_f32");
+  return VR_OK;
+}
+
+}  // namespace vr

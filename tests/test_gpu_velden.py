@@ -1,0 +1,118 @@
+"""Local velocity density f_l (Sec. 2.2) on the GPU vs the FP64 oracle.
+
+Position neighbour sets are exact (integer keys), so f_l differs only by FP32 rounding
+of velocity differences and sums: the bar is 1e-4 relative.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from helpers import assert_close_nan, oracle_fl
+
+pytestmark = pytest.mark.gpu
+RTOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1902_01010_gb300 import Context
+
+    return Context(0)
+
+
+def _gpu_fl(ctx, pos, vel, label, **kw):
+    from paper_1902_01010_gb300 import Params
+
+    P = Params.default(**kw)
+    f = ctx.velden(torch.from_numpy(np.ascontiguousarray(pos)).cuda(),
+                   torch.from_numpy(np.ascontiguousarray(vel)).cuda(),
+                   torch.from_numpy(np.ascontiguousarray(label, np.int32)).cuda(), P)
+    ctx.sync()
+    return f.cpu().numpy()
+
+
+def test_small_box(ctx):
+    box = synth.named("c32")
+    lab = oracle.fof3d(box.pos, box.link_d2)
+    got = _gpu_fl(ctx, box.pos, box.vel, lab)
+    ref = oracle_fl(box.pos, box.vel, lab)
+    assert np.isfinite(ref).sum() > 10000
+    assert_close_nan(got, ref, RTOL, what="f_l c32")
+
+
+def test_mass_function_box(ctx):
+    box = synth.named("m64")
+    lab = oracle.fof3d(box.pos, box.link_d2)
+    got = _gpu_fl(ctx, box.pos, box.vel, lab)
+    ref = oracle_fl(box.pos, box.vel, lab)
+    assert_close_nan(got, ref, RTOL, what="f_l m64")
+
+
+def _one_halo(nh, seed, spread=30000, coincident=0, center=(1000, 2000, 3000)):
+    rng = np.random.default_rng(seed)
+    p = np.array(center) + rng.normal(0, spread, size=(nh, 3))
+    pos = (np.round(p).astype(np.int64) % (1 << 21)).astype(np.int32)
+    if coincident:
+        pos[:coincident] = pos[0]
+    vel = rng.normal(0, 80, size=(nh, 3)).astype(np.float32)
+    return pos, vel, np.zeros(nh, np.int32)
+
+
+@pytest.mark.parametrize("nh", [20, 31, 32, 33, 255, 256, 257, 300, 1000, 5000])
+def test_halo_sizes_around_nse(ctx, nh):
+    pos, vel, lab = _one_halo(nh, nh)
+    assert_close_nan(_gpu_fl(ctx, pos, vel, lab), oracle_fl(pos, vel, lab), RTOL, what=f"nh={nh}")
+
+
+def test_ties_coincident_and_wrap(ctx):
+    # 400 coincident particles (d^2 ties broken by index) in a halo crossing the box edge
+    pos, vel, lab = _one_halo(3000, 5, spread=2000, coincident=400, center=(0, 0, 0))
+    assert_close_nan(_gpu_fl(ctx, pos, vel, lab), oracle_fl(pos, vel, lab), RTOL, what="ties")
+
+
+@pytest.mark.parametrize("nse,nv", [(64, 16), (100, 7), (512, 64), (1, 1), (32, 32)])
+def test_other_parameters(ctx, nse, nv):
+    pos, vel, lab = _one_halo(3000, 77)
+    got = _gpu_fl(ctx, pos, vel, lab, nse=nse, nv=nv)
+    assert_close_nan(got, oracle_fl(pos, vel, lab, nse, nv), RTOL, what=f"{nse},{nv}")
+
+
+def test_dense_cusp(ctx):
+    # a cuspy clump: thousands of particles inside a few lattice units
+    rng = np.random.default_rng(3)
+    r = rng.random(20000) ** 3 * 20000
+    d = rng.normal(size=(20000, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    pos = (np.round(d * r[:, None]).astype(np.int64) + 500000).astype(np.int32)
+    vel = rng.normal(0, 50, size=(20000, 3)).astype(np.float32)
+    lab = np.zeros(20000, np.int32)
+    assert_close_nan(_gpu_fl(ctx, pos, vel, lab), oracle_fl(pos, vel, lab), RTOL, what="cusp")
+
+
+def test_non_halo_particles_are_nan(ctx):
+    pos, vel, _ = _one_halo(100, 1)
+    lab = np.arange(100, dtype=np.int32)  # all singletons
+    assert np.all(np.isnan(_gpu_fl(ctx, pos, vel, lab)))
+
+
+@pytest.mark.slow
+def test_256cubed_sampled(ctx):
+    """Full 256^3 box in the benchmark's launch form; 3000 sampled members (biased to
+    the largest halos) computed one by one by the oracle."""
+    box = synth.named("c256")
+    lab = oracle.fof3d(box.pos, box.link_d2)
+    got = _gpu_fl(ctx, box.pos, box.vel, lab)
+    off, mem = oracle.halos(lab, 20)
+    sizes = np.diff(off)
+    rng = np.random.default_rng(0)
+    order = np.argsort(-sizes)
+    hs = list(order[:5]) + list(rng.choice(len(sizes), 40, replace=False))
+    for h in hs:
+        m = mem[off[h]:off[h + 1]]
+        up = oracle.unwrap(box.pos, m)
+        for k in rng.choice(len(m), min(60, len(m)), replace=False):
+            ref = oracle.velden_one(up, box.vel, m, int(k))
+            assert abs(got[m[k]] - ref) <= RTOL * ref, (h, k, got[m[k]], ref)
+    assert np.isnan(got[np.setdiff1d(np.arange(box.n), mem)]).all()
