@@ -5,20 +5,20 @@
 //  - halo members are Morton-ordered inside their halo (halos.cu); each run of 32
 //    consecutive members is a "bucket" with an integer bounding box, and 32 consecutive
 //    buckets of one halo form a "super-bucket";
-//  - one warp handles one bucket: lane k is the query particle k. An upper bound R_k on
-//    the N_se-th neighbour distance comes from the N_se members around the bucket in
-//    Morton order; every pass then visits the buckets whose boxes come within the
-//    largest per-lane bound of the warp's own box (super-bucket boxes prune first), and
-//    each pass tightens the per-lane bounds;
-//  - the candidates stream through the warp 32 at a time (one coalesced int4 load, then
-//    register shuffles), and every lane keeps its own 64-bin histogram of the exact key
-//    (d^2 << 22 | local index) in shared memory. Histogram passes narrow the key range
-//    until the bin holding the N_se-th key has at most 32 keys; a last pass feeds every
-//    key below that bin, plus the right number from the bin, into a per-lane list of the
-//    N_v smallest |dv|^2 (shared memory);
+//  - one warp handles one bucket: lane k is the query particle k. Each lane first bounds
+//    its N_se-th neighbour distance by the N_se-th smallest distance among the 4 N_se
+//    members around the bucket in Morton order (to within one of 32 histogram bins);
+//    every later pass visits only the buckets whose boxes come within the largest
+//    per-lane bound of the warp's own box (super-bucket boxes prune first);
+//  - each visited bucket is staged once in shared memory and read back by every lane
+//    with broadcast 16-byte loads; every lane keeps its own 32-bin histogram of the exact
+//    key (d^2 << 22 | local index). Histogram passes narrow the key range until the bin
+//    holding the N_se-th key has at most 16 keys; a last pass feeds every key below that
+//    bin, plus the right number from the bin, into a per-lane list of the N_v smallest
+//    |dv|^2 (shared memory);
 //  - h^2 is the largest kept |dv|^2, and the kernel sum runs over the kept list only
 //    (every neighbour with |dv| < h is in it).
-// Position keys are exact integers, so the N_se set equals the oracle's; velocities
+// Position keys are exact integers, so the N_se set equals the oracle's; velocity
 // differences and sums are FP32.
 // Halos with at most N_se members use every member (one pass, no position search).
 #include <math.h>
@@ -31,19 +31,25 @@ namespace vr {
 namespace {
 
 constexpr int kNVMax = 64;
-constexpr int kBins = 64;
-constexpr int kBuf = 32;
+constexpr int kBins = 32;
+constexpr int kBuf = 16;
 constexpr int kWarps = 4;        // warps per block
+constexpr int kWindow = 4;       // window of kWindow * N_se members for the first bound
 
+template <int NVM>
 struct WarpSmem {
+  int4 su[32];
+  float4 sv[32];
   uint16_t hist[kBins][32];
   u64 bkey[kBuf][32];
   float bdv[kBuf][32];
-  float top[kNVMax][32];
+  float top[NVM][32];
 };
 
+template <int NVM>
 struct SmallSmem {
-  float top[kNVMax][32];
+  float4 sv[32];
+  float top[NVM][32];
 };
 
 // Per-lane list of the nv smallest values (unsorted) with its current maximum.
@@ -104,10 +110,11 @@ __device__ __forceinline__ long long d2i(int4 a, int4 b) {
 }
 
 // ---------------------------------------------------------------- small halos
+template <int NVM>
 __global__ void __launch_bounds__(32 * kWarps) k_velden_small(
-    const uint32_t *__restrict__ hoff, const uint32_t *__restrict__ hlabel, int64_t H,
-    const float4 *__restrict__ v, int nse, int nv, float *__restrict__ f_l) {
-  __shared__ SmallSmem sm[kWarps];
+    const uint32_t *__restrict__ hoff, int64_t H, const float4 *__restrict__ v, int nse, int nv,
+    float *__restrict__ f_l) {
+  __shared__ SmallSmem<NVM> sm[kWarps];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   int64_t h = (int64_t)blockIdx.x * kWarps + w;
   if (h >= H) return;
@@ -123,19 +130,15 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_small(
     TopV t = {0, 0, 0.0f};
     for (uint32_t jb = hs; jb < he; jb += 32) {
       const uint32_t j = jb + lane;
-      const float4 vj = v[j < he ? j : hs];
+      __syncwarp();
+      if (j < he) sm[w].sv[lane] = v[j];
+      __syncwarp();
       const int cnt = (int)min(32u, he - jb);
-      for (int tt = 0; tt < cnt; ++tt) {
-        float4 vt;
-        vt.x = __shfl_sync(0xffffffffu, vj.x, tt);
-        vt.y = __shfl_sync(0xffffffffu, vj.y, tt);
-        vt.z = __shfl_sync(0xffffffffu, vj.z, tt);
-        if (valid) top_insert(top, lane, t, nv_eff, dv2f(vt, vq));
-      }
+      if (valid)
+        for (int tt = 0; tt < cnt; ++tt) top_insert(top, lane, t, nv_eff, dv2f(sm[w].sv[tt], vq));
     }
     if (valid) f_l[__float_as_int(vq.w)] = top_density(top, lane, t, nh);
   }
-  (void)hlabel;
 }
 
 // ------------------------------------------------------------- bucket boxes
@@ -214,6 +217,7 @@ __device__ __forceinline__ long long pt_box_d2(int4 p, int4 blo, int4 bhi) {
 __device__ __forceinline__ int bitlen64(unsigned long long x) { return x ? 64 - __clzll(x) : 0; }
 
 // ---------------------------------------------------------------- big halos
+template <int NVM>
 __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
     const uint32_t *__restrict__ hoff, const uint32_t *__restrict__ sboff,
     const uint32_t *__restrict__ sbhalo, int64_t nbpad, const int4 *__restrict__ u,
@@ -221,7 +225,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
     const int4 *__restrict__ smin, const int4 *__restrict__ smax, int nse, int nv,
     float *__restrict__ f_l, DevStatus *st) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  WarpSmem &sm = reinterpret_cast<WarpSmem *>(smem_raw)[threadIdx.x >> 5];
+  WarpSmem<NVM> &sm = reinterpret_cast<WarpSmem<NVM> *>(smem_raw)[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   const unsigned FULL = 0xffffffffu;
   const int64_t b = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
@@ -239,25 +243,60 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
   const float4 vq = v[valid ? k : qs];
   const int nse_eff = nse;  // nh > nse here
   const int nv_eff = nv;
-  // 1. bound from the N_se members around the bucket in Morton order
+  auto warp_max = [&](long long x) {
+    for (int o = 16; o; o >>= 1) {
+      long long y = __shfl_xor_sync(FULL, x, o);
+      x = y > x ? y : x;
+    }
+    return x;
+  };
+  // stages slots [s0, s0 + cnt) in shared memory (positions; velocities if asked)
+  auto stage = [&](uint32_t s0, int cnt, bool with_v) {
+    __syncwarp();
+    if (lane < cnt) {
+      sm.su[lane] = u[s0 + lane];
+      if (with_v) sm.sv[lane] = v[s0 + lane];
+    }
+    __syncwarp();
+  };
+  // 1. bound from the window of kWindow * N_se members around the bucket: the N_se-th
+  //    smallest distance among them, rounded up to a histogram bin edge
   long long r2 = 0;
   {
-    int64_t w0 = (int64_t)qs + 16 - nse / 2;
-    if (w0 + nse > (int64_t)he) w0 = (int64_t)he - nse;
+    const int W = (int)min((uint32_t)(kWindow * nse), nh);
+    int64_t w0 = (int64_t)qs + 16 - W / 2;
+    if (w0 + W > (int64_t)he) w0 = (int64_t)he - W;
     if (w0 < (int64_t)hs) w0 = hs;
-    for (int c = 0; c < nse; c += 32) {
-      int64_t j = w0 + c + lane;
-      int4 p = u[j < w0 + nse ? j : w0];
-      int cnt = min(32, nse - c);
+    long long wmax = 0;
+    for (int c = 0; c < W; c += 32) {
+      const int cnt = min(32, W - c);
+      stage((uint32_t)(w0 + c), cnt, false);
       for (int t = 0; t < cnt; ++t) {
-        int4 pt;
-        pt.x = __shfl_sync(FULL, p.x, t);
-        pt.y = __shfl_sync(FULL, p.y, t);
-        pt.z = __shfl_sync(FULL, p.z, t);
-        long long d = d2i(q, pt);
-        r2 = d > r2 ? d : r2;
+        long long d = d2i(q, sm.su[t]);
+        wmax = d > wmax ? d : wmax;
       }
     }
+    for (int cb = 0; cb < kBins; ++cb) sm.hist[cb][lane] = 0;
+    int sh0 = bitlen64((unsigned long long)wmax) - 5;  // 32 bins over [0, 2^bitlen)
+    if (sh0 < 0) sh0 = 0;
+    for (int c = 0; c < W; c += 32) {
+      const int cnt = min(32, W - c);
+      stage((uint32_t)(w0 + c), cnt, false);
+      for (int t = 0; t < cnt; ++t) {
+        long long d = d2i(q, sm.su[t]);
+        sm.hist[(unsigned)(d >> sh0)][lane]++;
+      }
+    }
+    int cum = 0, bs = kBins - 1;
+    for (int cb = 0; cb < kBins; ++cb) {
+      cum += sm.hist[cb][lane];
+      if (cum >= nse_eff) {
+        bs = cb;
+        break;
+      }
+    }
+    r2 = (((long long)bs + 1) << sh0) - 1;  // every distance in bins <= bs is <= r2
+    if (r2 > wmax) r2 = wmax;
   }
   if (r2 >= (1LL << 41)) {
     raise_error(st, VR_ERR_UNSUPPORTED, 1);
@@ -265,7 +304,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
   }
   // Candidate buckets are enumerated on the fly in every pass: super-bucket boxes, then
   // bucket boxes, against the query bucket's box grown by the largest per-lane bound;
-  // f(bucket_slot_start) is called warp-uniformly for every bucket that passes.
+  // f(bucket index) is called warp-uniformly for every bucket that passes.
   const int4 qlo = bmin[b], qhi = bmax[b];
   const uint32_t sb0 = sboff[h], sb1 = sboff[h + 1];
   auto for_each_bucket = [&](long long rmax2, auto &&f) {
@@ -287,39 +326,28 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
       }
     }
   };
-  auto warp_max = [&](long long x) {
-    for (int o = 16; o; o >>= 1) {
-      long long y = __shfl_xor_sync(FULL, x, o);
-      x = y > x ? y : x;
-    }
-    return x;
-  };
   // 2. histogram passes over the exact keys (d^2 << 22 | local index)
   u64 klo = 0;
-  int sh = bitlen64(((u64)(r2 + 1) << 22) - 1) - 6;
+  int sh = bitlen64(((u64)(r2 + 1) << 22) - 1) - 5;
   if (sh < 0) sh = 0;
   int need = nse_eff;
   bool settled = !valid;
   u64 fin_lo = 0, fin_hi = 0;
   int need_in = 0;
   long long rcur = r2;  // per-lane bound on d^2 of keys still of interest
-  for (int level = 0; level < 12; ++level) {
+  for (int level = 0; level < 16; ++level) {
     if (!settled)
       for (int c = 0; c < kBins; ++c) sm.hist[c][lane] = 0;
-    const long long rmax2 = warp_max(settled ? 0 : rcur);
+    const long long rmax2 = warp_max(settled ? -1 : rcur);
     for_each_bucket(rmax2, [&](uint32_t bb) {
       bool want = !settled && pt_box_d2(q, bmin[bb], bmax[bb]) <= rcur;
       if (!__any_sync(FULL, want)) return;
       const uint32_t s0 = hs + 32u * (bb - 32u * sb0);
       const int cnt = (int)min(32u, he - s0);
-      const int4 p = u[s0 + (lane < cnt ? lane : 0)];
-      for (int t = 0; t < cnt; ++t) {
-        int4 pt;
-        pt.x = __shfl_sync(FULL, p.x, t);
-        pt.y = __shfl_sync(FULL, p.y, t);
-        pt.z = __shfl_sync(FULL, p.z, t);
-        pt.w = __shfl_sync(FULL, p.w, t);
-        if (want) {
+      stage(s0, cnt, false);
+      if (want) {
+        for (int t = 0; t < cnt; ++t) {
+          const int4 pt = sm.su[t];
           long long d = d2i(q, pt);
           if (d <= rcur) {
             u64 key = ((u64)d << 22) | (u64)pt.w;
@@ -352,7 +380,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
         need -= cum;
         const long long top_d = (long long)((klo + ((u64)1 << sh) - 1) >> 22);
         rcur = top_d < rcur ? top_d : rcur;
-        sh = sh >= 6 ? sh - 6 : 0;
+        sh = sh >= 5 ? sh - 5 : 0;
       }
     }
     if (__all_sync(FULL, settled)) break;
@@ -372,27 +400,18 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
     if (!__any_sync(FULL, want)) return;
     const uint32_t s0 = hs + 32u * (bb - 32u * sb0);
     const int cnt = (int)min(32u, he - s0);
-    const int4 p = u[s0 + (lane < cnt ? lane : 0)];
-    const float4 pv = v[s0 + (lane < cnt ? lane : 0)];
-    for (int t = 0; t < cnt; ++t) {
-      int4 pt;
-      float4 vt;
-      pt.x = __shfl_sync(FULL, p.x, t);
-      pt.y = __shfl_sync(FULL, p.y, t);
-      pt.z = __shfl_sync(FULL, p.z, t);
-      pt.w = __shfl_sync(FULL, p.w, t);
-      vt.x = __shfl_sync(FULL, pv.x, t);
-      vt.y = __shfl_sync(FULL, pv.y, t);
-      vt.z = __shfl_sync(FULL, pv.z, t);
-      if (want) {
+    stage(s0, cnt, true);
+    if (want) {
+      for (int t = 0; t < cnt; ++t) {
+        const int4 pt = sm.su[t];
         long long d = d2i(q, pt);
         if (d <= rcur) {
           u64 key = ((u64)d << 22) | (u64)pt.w;
           if (key < fin_lo) {
-            top_insert(top, lane, tv, nv_eff, dv2f(vt, vq));
+            top_insert(top, lane, tv, nv_eff, dv2f(sm.sv[t], vq));
           } else if (key < fin_hi && nbuf < kBuf) {
             sm.bkey[nbuf][lane] = key;
-            sm.bdv[nbuf][lane] = dv2f(vt, vq);
+            sm.bdv[nbuf][lane] = dv2f(sm.sv[t], vq);
             ++nbuf;
           }
         }
@@ -457,8 +476,13 @@ vr_status run_velden(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Arena &a
   if (!ar.ok()) return set_error(ctx, VR_ERR_WORKSPACE_TOO_SMALL, "workspace too small");
   const int T = 256;
   // small halos: all members are neighbours
-  VR_TIMED(ctx, "velden_small", s, k_velden_small<<<grid_for(H, kWarps), 32 * kWarps, 0, s>>>(g.hoff, g.hlabel, H, g.v, p->nse,
-                                                            p->nv, f_l));
+  if (p->nv <= 32) {
+    VR_TIMED(ctx, "velden_small", s, k_velden_small<32><<<grid_for(H, kWarps), 32 * kWarps, 0, s>>>(
+        g.hoff, H, g.v, p->nse, p->nv, f_l));
+  } else {
+    VR_TIMED(ctx, "velden_small", s, k_velden_small<kNVMax><<<grid_for(H, kWarps), 32 * kWarps, 0, s>>>(
+        g.hoff, H, g.v, p->nse, p->nv, f_l));
+  }
   VR_LAUNCHED(ctx, "k_velden_small");
   k_sb_count<<<grid_for(H + 1, T), T, 0, s>>>(g.hoff, H, p->nse, sboff);
   VR_LAUNCHED(ctx, "k_sb_count");
@@ -476,11 +500,19 @@ vr_status run_velden(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Arena &a
   VR_LAUNCHED(ctx, "k_bucket_boxes");
   k_superbucket_boxes<<<grid_for(nsb, T), T, 0, s>>>(nsb, bmin, bmax, smin, smax);
   VR_LAUNCHED(ctx, "k_superbucket_boxes");
-  size_t shm = sizeof(WarpSmem) * kWarps;
-  VR_CUDA(ctx, cudaFuncSetAttribute(k_velden_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-  VR_TIMED(ctx, "velden_big", s, k_velden_big<<<grid_for(nbpad, kWarps), 32 * kWarps, shm, s>>>(
-      g.hoff, sboff, sbhalo, nbpad, g.u, g.v, bmin, bmax, smin, smax, p->nse, p->nv, f_l,
-      ctx->d_status));
+  if (p->nv <= 32) {
+    size_t shm = sizeof(WarpSmem<32>) * kWarps;
+    VR_CUDA(ctx, cudaFuncSetAttribute(k_velden_big<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    VR_TIMED(ctx, "velden_big", s, k_velden_big<32><<<grid_for(nbpad, kWarps), 32 * kWarps, shm, s>>>(
+        g.hoff, sboff, sbhalo, nbpad, g.u, g.v, bmin, bmax, smin, smax, p->nse, p->nv, f_l,
+        ctx->d_status));
+  } else {
+    size_t shm = sizeof(WarpSmem<kNVMax>) * kWarps;
+    VR_CUDA(ctx, cudaFuncSetAttribute(k_velden_big<kNVMax>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    VR_TIMED(ctx, "velden_big", s, k_velden_big<kNVMax><<<grid_for(nbpad, kWarps), 32 * kWarps, shm, s>>>(
+        g.hoff, sboff, sbhalo, nbpad, g.u, g.v, bmin, bmax, smin, smax, p->nse, p->nv, f_l,
+        ctx->d_status));
+  }
   VR_LAUNCHED(ctx, "k_velden_big");
   return VR_OK;
 }

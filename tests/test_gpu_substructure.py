@@ -4,7 +4,8 @@ Each stage is compared on the same inputs (Sec. 2.2):
   - R: the oracle's background model is fed the GPU's f_l, so only the cells, moments,
     interpolation and Cholesky are under test; bar |dR| <= 1e-4 max(1, |R|);
   - fit: the oracle's fit is fed the GPU's R; histogram counts are then identical and the
-    Levenberg-Marquardt results agree to rounding (1e-9 relative);
+    Levenberg-Marquardt results agree to 1e-7 relative: the fit stops on a relative cost
+    change below 1e-15, which fixes the parameters only to about sqrt(1e-15) ~ 3e-8;
   - 6D labels: the oracle's linker is fed the GPU's outlier mask and per-halo parameters;
     labels must be bit-identical.
 The end-to-end test runs both pipelines independently and lists threshold flips.
@@ -108,8 +109,8 @@ def test_fit_and_ell_match_oracle_fit(staged):
             continue
         fit = oracle.ell_fit(g["R"][m].astype(np.float64))
         rbar, sig = g["hs"][h, 3], g["hs"][h, 4]
-        assert abs(rbar - fit[0]) <= 1e-9 * max(1.0, abs(fit[0])), (h, rbar, fit[0])
-        assert abs(sig - fit[1]) <= 1e-9 * fit[1], (h, sig, fit[1])
+        assert abs(rbar - fit[0]) <= 1e-7 * max(1.0, abs(fit[0])), (h, rbar, fit[0])
+        assert abs(sig - fit[1]) <= 1e-7 * fit[1], (h, sig, fit[1])
         e = (g["R"][m].astype(np.float64) - rbar) / sig
         assert np.allclose(g["ell"][m], e, rtol=1e-6, atol=1e-6, equal_nan=True)
 
@@ -206,13 +207,13 @@ def test_no_searched_halos(ctx):
 
 
 def test_degenerate_cells_give_nan(ctx):
-    """A halo whose particles all share one velocity: every cell's tensor is zero, so R is
-    NaN (not PD) everywhere and the fit is degenerate."""
+    """A halo whose particles all share one velocity: every cell's dispersion tensor is
+    exactly zero, so no Cholesky factor exists and R is NaN for every member (the call
+    does not abort); the fit of such a halo is degenerate and ell is NaN too."""
     rng = np.random.default_rng(2)
     n = 400
     pos = (np.round(rng.normal(0, 200, size=(n, 3))).astype(np.int64) + 10000).astype(np.int32)
     vel = np.tile(np.array([[10.0, 20.0, 30.0]], np.float32), (n, 1))
-    vel[:5] += np.float32(1.0)  # velden needs h > 0 for most particles
     from paper_1902_01010_gb300 import Params
 
     P = Params.default()
@@ -221,5 +222,7 @@ def test_degenerate_cells_give_nan(ctx):
     fl = ctx.velden(p, v, lab, P)
     R, ell, hs = ctx.outlier_ratio(p, v, fl, lab, P)
     ctx.sync()
-    R = R.cpu().numpy()
-    assert np.isnan(R).sum() >= n - 10
+    assert np.isinf(fl.cpu().numpy()).all()  # h = 0: every velocity neighbour coincides
+    assert np.isnan(R.cpu().numpy()).all()
+    assert np.isnan(ell.cpu().numpy()).all()
+    assert hs.shape[0] == 1 and math.isnan(hs[0, 4].item())
