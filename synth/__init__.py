@@ -123,17 +123,20 @@ def mass_function_box(n: int, seed: int) -> Box:
                     conc_hi=15.0, sigma_host=100.0, sigma_bg=30.0, name=f"massfn_{n}")
 
 
-def named(name: str) -> Box:
-    """The standard workloads: 32^3 clustered, 256^3 / 512^3 / 1024^3 mass-function boxes."""
+def named(name: str, replica: int = 0) -> Box:
+    """The standard workloads: 32^3 clustered, 256^3 / 512^3 / 1024^3 mass-function boxes,
+    and m<k> = a k^3 mass-function box. `replica` > 0 draws an independent box of the same
+    kind (another seed)."""
+    r = 100000 * replica
     if name == "c32":
-        return small_clustered(32 ** 3, SEED0 + 0)
+        return small_clustered(32 ** 3, SEED0 + 0 + r)
     if name == "c256":
-        return mass_function_box(256 ** 3, SEED0 + 1)
+        return mass_function_box(256 ** 3, SEED0 + 1 + r)
     if name == "c512":
-        return mass_function_box(512 ** 3, SEED0 + 2)
+        return mass_function_box(512 ** 3, SEED0 + 2 + r)
     if name == "c1024":
-        return mass_function_box(1024 ** 3, SEED0 + 4)
+        return mass_function_box(1024 ** 3, SEED0 + 4 + r)
     if name.startswith("m") and name[1:].isdigit():
         m = int(name[1:])
-        return mass_function_box(m ** 3, SEED0 + 10 + m)
+        return mass_function_box(m ** 3, SEED0 + 10 + m + r)
     raise KeyError(name)
