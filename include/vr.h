@@ -181,6 +181,28 @@ vr_status vr_find_substructure(vr_ctx *ctx, const int32_t *pos, const float *vel
                                float *ell, int32_t *label6, double *halo_stats, int64_t *nhalo,
                                void *ws, size_t ws_bytes, void *stream);
 
+/* ----------------------------------------------------- allocation-free 3D FOF
+ * No counterpart in the paper. For callers that cannot allocate device memory at all
+ * (for example code running where cudaMalloc is forbidden or unavailable, such as inside
+ * another library's allocation-free section, or a host that has handed all device
+ * memory to its own pool): the same result as vr_fof3d, but with no context, no
+ * workspace argument and no allocation. Its scratch is one static device array of
+ * VR_FOF3D_NOALLOC_BYTES bytes compiled into this library, which every GPU that loads
+ * the library holds until the process exits.
+ *   pos, n, link_d2, label: as for vr_fof3d, with n <= VR_FOF3D_NOALLOC_MAX_N
+ *   stream: cudaStream_t on the current device (NULL = legacy default stream)
+ * Works on the calling thread's current device. The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before any stream
+ * capture. All calls share the one array and every call overwrites it: calls whose
+ * work overlaps on the GPU (other streams, or host threads on the same device) race and
+ * must be serialised by the caller. Returns VR_ERR_INVALID_ARG for n above the maximum
+ * or bad arguments, VR_ERR_CUDA if the address lookup or a launch fails; the status code
+ * is the only error report. */
+#define VR_FOF3D_NOALLOC_MAX_N 131072
+#define VR_FOF3D_NOALLOC_BYTES (8u << 20)
+vr_status vr_fof3d_noalloc(const int32_t *pos, int64_t n, int64_t link_d2, int32_t *label,
+                           void *stream);
+
 /* ---------------------------------------------------------------- measurement
  * (no counterpart in the paper: instrumentation of this library)
  * Per-kernel device timing with CUDA events recorded on the launching stream; off by
