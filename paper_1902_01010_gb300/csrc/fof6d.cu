@@ -187,6 +187,8 @@ __global__ void __launch_bounds__(128) k_link6(const uint32_t *__restrict__ toff
       if (tj == (uint32_t)ti && k <= (uint32_t)lane) continue;  // each pair once
       long long dx = (long long)pa.x - p.x, dy = (long long)pa.y - p.y, dz = (long long)pa.z - p.z;
       long long dx2 = dx * dx + dy * dy + dz * dz;
+      // exact pre-test: dx2 >= lx2 gives dx2 / lx2 >= 1 after rounding, so q >= 1
+      if ((double)dx2 >= L.lx2) continue;
       if (link6(dx2, qa, q, L)) uf_unite(parent, (int)(ia + lane), (int)(ib + k));
     }
   }

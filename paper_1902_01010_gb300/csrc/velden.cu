@@ -34,6 +34,16 @@ constexpr int kNVMax = 64;
 constexpr int kBins = 32;
 constexpr int kBuf = 16;
 constexpr int kWarps = 4;        // warps per block
+
+// Optional instrumentation (compile with -DVR_VELDEN_STATS): warp-level counts of the
+// buckets staged per pass, kept in the status block's info[] words. Off in normal builds.
+constexpr int kStatPass0 = 1;    // info[1 + pass]: 0 window, 1.. histogram levels, 7 collect
+#ifdef VR_VELDEN_STATS
+#define VR_STAT(st, slot, val) \
+  do { if ((threadIdx.x & 31) == 0) atomicAdd((unsigned long long *)&(st)->info[(slot)], (unsigned long long)(val)); } while (0)
+#else
+#define VR_STAT(st, slot, val) do { } while (0)
+#endif
 constexpr int kWindow = 4;       // window of kWindow * N_se members for the first bound
 
 template <int NVM>
@@ -243,6 +253,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
   const float4 vq = v[valid ? k : qs];
   const int nse_eff = nse;  // nh > nse here
   const int nv_eff = nv;
+  int pass_id = 0;  // instrumentation only
   auto warp_max = [&](long long x) {
     for (int o = 16; o; o >>= 1) {
       long long y = __shfl_xor_sync(FULL, x, o);
@@ -250,14 +261,19 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
     }
     return x;
   };
-  // stages slots [s0, s0 + cnt) in shared memory (positions; velocities if asked)
+  // stages slots [s0, s0 + cnt) in shared memory (positions; velocities if asked); the
+  // remaining entries get a sentinel position far outside any bound (d^2 > 2^58), so the
+  // candidate loops always run 32 fixed iterations
   auto stage = [&](uint32_t s0, int cnt, bool with_v) {
     __syncwarp();
     if (lane < cnt) {
       sm.su[lane] = u[s0 + lane];
       if (with_v) sm.sv[lane] = v[s0 + lane];
+    } else {
+      sm.su[lane] = make_int4(0x3fffffff, 0x3fffffff, 0x3fffffff, 0);
     }
     __syncwarp();
+    VR_STAT(st, kStatPass0 + pass_id, 1);
   };
   // 1. bound from the window of kWindow * N_se members around the bucket: the N_se-th
   //    smallest distance among them, rounded up to a histogram bin edge
@@ -271,9 +287,12 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
     for (int c = 0; c < W; c += 32) {
       const int cnt = min(32, W - c);
       stage((uint32_t)(w0 + c), cnt, false);
-      for (int t = 0; t < cnt; ++t) {
-        long long d = d2i(q, sm.su[t]);
-        wmax = d > wmax ? d : wmax;
+      for (int t0 = 0; t0 < 32; t0 += 8) {
+        long long d[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) d[j] = d2i(q, sm.su[t0 + j]);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) wmax = (t0 + j < cnt && d[j] > wmax) ? d[j] : wmax;
       }
     }
     for (int cb = 0; cb < kBins; ++cb) sm.hist[cb][lane] = 0;
@@ -282,9 +301,13 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
     for (int c = 0; c < W; c += 32) {
       const int cnt = min(32, W - c);
       stage((uint32_t)(w0 + c), cnt, false);
-      for (int t = 0; t < cnt; ++t) {
-        long long d = d2i(q, sm.su[t]);
-        sm.hist[(unsigned)(d >> sh0)][lane]++;
+      for (int t0 = 0; t0 < 32; t0 += 8) {
+        long long d[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) d[j] = d2i(q, sm.su[t0 + j]);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (t0 + j < cnt) sm.hist[(unsigned)(d[j] >> sh0)][lane]++;
       }
     }
     int cum = 0, bs = kBins - 1;
@@ -336,6 +359,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
   int need_in = 0;
   long long rcur = r2;  // per-lane bound on d^2 of keys still of interest
   for (int level = 0; level < 16; ++level) {
+    pass_id = level < 5 ? 1 + level : 5;
     if (!settled)
       for (int c = 0; c < kBins; ++c) sm.hist[c][lane] = 0;
     const long long rmax2 = warp_max(settled ? -1 : rcur);
@@ -346,14 +370,18 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
       const int cnt = (int)min(32u, he - s0);
       stage(s0, cnt, false);
       if (want) {
-        for (int t = 0; t < cnt; ++t) {
-          const int4 pt = sm.su[t];
-          long long d = d2i(q, pt);
-          if (d <= rcur) {
-            u64 key = ((u64)d << 22) | (u64)pt.w;
-            if (key >= klo) {
-              u64 rel = (key - klo) >> sh;
-              if (rel < kBins) sm.hist[rel][lane]++;
+        for (int t0 = 0; t0 < 32; t0 += 8) {
+          long long d[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) d[j] = d2i(q, sm.su[t0 + j]);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            if (d[j] <= rcur) {
+              u64 key = ((u64)d[j] << 22) | (u64)sm.su[t0 + j].w;
+              if (key >= klo) {
+                u64 rel = (key - klo) >> sh;
+                if (rel < kBins) sm.hist[rel][lane]++;
+              }
             }
           }
         }
@@ -395,6 +423,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
   float(*top)[32] = sm.top;
   TopV tv = {0, 0, 0.0f};
   int nbuf = 0;
+  pass_id = 6;
   for_each_bucket(warp_max(rcur), [&](uint32_t bb) {
     bool want = valid && pt_box_d2(q, bmin[bb], bmax[bb]) <= rcur;
     if (!__any_sync(FULL, want)) return;
@@ -402,17 +431,22 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
     const int cnt = (int)min(32u, he - s0);
     stage(s0, cnt, true);
     if (want) {
-      for (int t = 0; t < cnt; ++t) {
-        const int4 pt = sm.su[t];
-        long long d = d2i(q, pt);
-        if (d <= rcur) {
-          u64 key = ((u64)d << 22) | (u64)pt.w;
-          if (key < fin_lo) {
-            top_insert(top, lane, tv, nv_eff, dv2f(sm.sv[t], vq));
-          } else if (key < fin_hi && nbuf < kBuf) {
-            sm.bkey[nbuf][lane] = key;
-            sm.bdv[nbuf][lane] = dv2f(sm.sv[t], vq);
-            ++nbuf;
+      for (int t0 = 0; t0 < 32; t0 += 8) {
+        long long d[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) d[j] = d2i(q, sm.su[t0 + j]);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (d[j] <= rcur) {
+            const int t = t0 + j;
+            u64 key = ((u64)d[j] << 22) | (u64)sm.su[t].w;
+            if (key < fin_lo) {
+              top_insert(top, lane, tv, nv_eff, dv2f(sm.sv[t], vq));
+            } else if (key < fin_hi && nbuf < kBuf) {
+              sm.bkey[nbuf][lane] = key;
+              sm.bdv[nbuf][lane] = dv2f(sm.sv[t], vq);
+              ++nbuf;
+            }
           }
         }
       }
