@@ -46,13 +46,19 @@ constexpr int kStatPass0 = 1;    // info[1 + pass]: 0 window, 1.. histogram leve
 #endif
 constexpr int kWindow = 4;       // window of kWindow * N_se members for the first bound
 
+// Per-warp shared memory. The key histogram is used only by the bound and histogram
+// passes and the final-bin buffer only by the collect pass, so the two share storage.
 template <int NVM>
 struct WarpSmem {
   int4 su[32];
   float4 sv[32];
-  uint16_t hist[kBins][32];
-  u64 bkey[kBuf][32];
-  float bdv[kBuf][32];
+  union {
+    uint16_t hist[kBins][32];
+    struct {
+      u64 bkey[kBuf][32];
+      float bdv[kBuf][32];
+    };
+  };
   float top[NVM][32];
 };
 
