@@ -28,6 +28,7 @@ namespace {
 
 constexpr int kTB = 256;           // threads per tree-building CTA
 constexpr int kMaxBins = 162;      // floor((2^22)^(1/3)) + 1
+constexpr int kSmallNode = 1024;   // nodes up to this size find their median by counting
 
 __device__ __forceinline__ int64_t ncell_of(int64_t nh, double f_cell, int ncell_min) {
   int64_t nc = (int64_t)floor(__dmul_rn(f_cell, (double)nh));
@@ -71,12 +72,13 @@ __device__ __forceinline__ int coord(const int4 &p, int a) { return a == 0 ? p.x
 
 // Halo table row for every halo (searched or not): FP64 frame and sigma_host.
 __global__ void __launch_bounds__(kTB) k_halo_frame(const uint32_t *__restrict__ hoff,
-                                                    const uint32_t *__restrict__ hlabel, int64_t H,
+                                                    const uint32_t *__restrict__ hlabel,
+                                                    const uint32_t *__restrict__ horder, int64_t H,
                                                     const float4 *__restrict__ v, int nsearch_min,
                                                     double *__restrict__ hs_out) {
   __shared__ double sd[kTB / 32];
-  const int64_t h = blockIdx.x;
-  if (h >= H) return;
+  if ((int64_t)blockIdx.x >= H) return;
+  const int64_t h = horder[blockIdx.x];  // largest halos first
   const uint32_t b = hoff[h], e = hoff[h + 1];
   const double nh = (double)(e - b);
   double s[3] = {0, 0, 0};
@@ -135,7 +137,8 @@ __global__ void k_node_caps(const uint32_t *__restrict__ hoff, int64_t H, int ns
 }
 
 __global__ void __launch_bounds__(kTB) k_cells_build(
-    const uint32_t *__restrict__ hoff, const uint32_t *__restrict__ nodeoff, int64_t H,
+    const uint32_t *__restrict__ hoff, const uint32_t *__restrict__ horder,
+    const uint32_t *__restrict__ nodeoff, int64_t H,
     const int4 *__restrict__ u, const float4 *__restrict__ v, int nsearch_min, double f_cell,
     int ncell_min, int split_rule, uint32_t *__restrict__ perm, uint32_t *__restrict__ tmp,
     CellNode *__restrict__ nodes, double *__restrict__ mom, uint32_t *__restrict__ leaf_of,
@@ -151,8 +154,10 @@ __global__ void __launch_bounds__(kTB) k_cells_build(
   __shared__ int s_rank;
   __shared__ int s_count;
   __shared__ uint32_t s_scan[kTB];
-  const int64_t h = blockIdx.x;
-  if (h >= H) return;
+  __shared__ unsigned long long s_keys[kSmallNode];
+  __shared__ uint32_t s_offl, s_offr;
+  if ((int64_t)blockIdx.x >= H) return;
+  const int64_t h = horder[blockIdx.x];  // largest halos first
   const uint32_t hb = hoff[h], he = hoff[h + 1];
   const int64_t nh = he - hb;
   if (nh < nsearch_min) return;
@@ -219,23 +224,28 @@ __global__ void __launch_bounds__(kTB) k_cells_build(
       }
     }
     __syncthreads();
+    // Shannon entropy per axis (Eq. S): every thread sums the bins it owns, then a block
+    // reduction; thread 0 orders the axes.
+    double Sa[3];
+    for (int a = 0; a < 3; ++a) {
+      double part = 0.0;
+      if (amax[a] > amin[a]) {
+        for (int b = t; b < nbins; b += kTB) {
+          int c = s_hist[a][b];
+          if (c > 0) {
+            double f = (double)c / (double)n;
+            part -= f * log(f);
+          }
+        }
+      }
+      Sa[a] = block_reduce(part, AddD(), s_rd);
+    }
     if (t == 0) {
       double S[3];
       int ok[3];
       for (int a = 0; a < 3; ++a) {
         ok[a] = amax[a] > amin[a];
-        S[a] = 0.0;
-        if (ok[a]) {
-          double s = 0.0;
-          for (int b = 0; b < nbins; ++b) {
-            int c = s_hist[a][b];
-            if (c > 0) {
-              double f = (double)c / (double)n;
-              s -= f * log(f);
-            }
-          }
-          S[a] = s / log((double)nbins);
-        }
+        S[a] = ok[a] ? Sa[a] / log((double)nbins) : 0.0;
       }
       int used[3] = {0, 0, 0}, no = 0;
       for (int r = 0; r < 3; ++r) {
@@ -257,49 +267,70 @@ __global__ void __launch_bounds__(kTB) k_cells_build(
     for (int r = 0; r < norder && !split_done; ++r) {
       const int a = s_order[r];
       const int lo_a = amin[a];
-      // radix select of the element of rank floor(n/2) by key ((x - lo) << 22 | local index)
-      int bits = 22;
-      {
-        unsigned int ext = (unsigned int)(amax[a] - lo_a);
-        while (ext) { ++bits; ext >>= 1; }
-      }
-      int ndig = (bits + 7) / 8;
-      if (t == 0) {
-        s_prefix = 0ULL;
-        s_rank = (int)(n / 2);
-      }
-      __syncthreads();
-      for (int d = ndig - 1; d >= 0; --d) {
-        s_dig[t] = 0;
+      // element of rank floor(n/2) by key ((x - lo) << 22 | local index); keys are unique
+      auto node_key = [&](uint32_t i) {
+        int4 p = u[perm[i]];
+        return ((unsigned long long)(coord(p, a) - lo_a) << 22) | (unsigned)p.w;
+      };
+      if (n <= kSmallNode) {
+        // small node: rank by counting, keys staged in shared memory
+        for (uint32_t i = nb_ + t; i < ne_; i += kTB) s_keys[i - nb_] = node_key(i);
         __syncthreads();
-        const int sh = 8 * d;
-        const unsigned long long pre = s_prefix;
-        for (uint32_t i = nb_ + t; i < ne_; i += kTB) {
-          int4 p = u[perm[i]];
-          unsigned long long key = ((unsigned long long)(coord(p, a) - lo_a) << 22) | (unsigned)p.w;
-          unsigned long long hiK = (sh + 8 >= 64) ? 0ULL : (key >> (sh + 8));
-          unsigned long long hiP = (sh + 8 >= 64) ? 0ULL : (pre >> (sh + 8));
-          if (hiK == hiP) atomicAdd(&s_dig[(key >> sh) & 0xffu], 1u);
+        const int target = (int)(n / 2);
+        for (int i = t; i < (int)n; i += kTB) {
+          const unsigned long long ki = s_keys[i];
+          int below = 0;
+          for (int j = 0; j < (int)n; ++j) below += s_keys[j] < ki ? 1 : 0;
+          if (below == target) s_prefix = ki;
         }
         __syncthreads();
-        // exclusive scan of the 256 digit counts; thread t owns digit t
-        uint32_t c = s_dig[t];
-        s_scan[t] = c;
+      } else {
+        // large node: 8-bit radix selection from the top digit
+        int bits = 22;
+        {
+          unsigned int ext = (unsigned int)(amax[a] - lo_a);
+          while (ext) { ++bits; ext >>= 1; }
+        }
+        int ndig = (bits + 7) / 8;
+        if (t == 0) {
+          s_prefix = 0ULL;
+          s_rank = (int)(n / 2);
+        }
         __syncthreads();
-        for (int o = 1; o < 256; o <<= 1) {
-          uint32_t x = t >= o ? s_scan[t - o] : 0u;
+        for (int d = ndig - 1; d >= 0; --d) {
+          s_dig[t] = 0;
           __syncthreads();
-          s_scan[t] += x;
+          const int sh = 8 * d;
+          const unsigned long long pre = s_prefix;
+          for (uint32_t i = nb_ + t; i < ne_; i += kTB) {
+            unsigned long long key = node_key(i);
+            unsigned long long hiK = (sh + 8 >= 64) ? 0ULL : (key >> (sh + 8));
+            unsigned long long hiP = (sh + 8 >= 64) ? 0ULL : (pre >> (sh + 8));
+            if (hiK == hiP) atomicAdd(&s_dig[(key >> sh) & 0xffu], 1u);
+          }
+          __syncthreads();
+          // exclusive scan of the 256 digit counts (thread t owns digit t): warp scans,
+          // then the 8 warp totals
+          const uint32_t c = s_dig[t];
+          uint32_t incl = c;
+          for (int o = 1; o < 32; o <<= 1) {
+            uint32_t x = __shfl_up_sync(0xffffffffu, incl, o);
+            if ((t & 31) >= o) incl += x;
+          }
+          if ((t & 31) == 31) s_scan[t >> 5] = incl;
+          __syncthreads();
+          uint32_t wbase = 0;
+          for (int w = 0; w < (t >> 5); ++w) wbase += s_scan[w];
+          incl += wbase;
+          const uint32_t excl = incl - c;
+          const int rk = s_rank;
+          __syncthreads();
+          if ((int)excl <= rk && rk < (int)incl) {
+            s_prefix = pre | ((unsigned long long)t << sh);
+            s_rank = rk - (int)excl;
+          }
           __syncthreads();
         }
-        uint32_t incl = s_scan[t], excl = incl - c;
-        const int rk = s_rank;
-        __syncthreads();
-        if ((int)excl <= rk && rk < (int)incl) {
-          s_prefix = pre | ((unsigned long long)t << sh);
-          s_rank = rk - (int)excl;
-        }
-        __syncthreads();
       }
       const int xs = lo_a + (int)(s_prefix >> 22);
       // left = {x < xs}
@@ -307,35 +338,40 @@ __global__ void __launch_bounds__(kTB) k_cells_build(
       for (uint32_t i = nb_ + t; i < ne_; i += kTB) cl += coord(u[perm[i]], a) < xs ? 1 : 0;
       const int nleft = block_reduce(cl, AddI(), s_ri);
       if (nleft == 0) continue;  // left side empty: next axis
-      // ordered partition into tmp, then back into perm
-      uint32_t offl = 0, offr = 0;
-      for (uint32_t cb = nb_; cb < ne_; cb += kTB) {
-        uint32_t i = cb + t;
-        uint32_t pm = 0;
-        int isl = 0;
-        if (i < ne_) {
-          pm = perm[i];
-          isl = coord(u[pm], a) < xs ? 1 : 0;
-        }
-        s_scan[t] = isl;
-        __syncthreads();
-        for (int o = 1; o < kTB; o <<= 1) {
-          uint32_t x = t >= o ? s_scan[t - o] : 0u;
-          __syncthreads();
-          s_scan[t] += x;
-          __syncthreads();
-        }
-        uint32_t incl = s_scan[t];
-        uint32_t totl = s_scan[kTB - 1];
-        uint32_t cnt = min((uint32_t)kTB, ne_ - cb);
-        if (i < ne_) {
-          if (isl) tmp[nb_ + offl + incl - 1] = pm;
-          else tmp[nb_ + nleft + offr + (t - incl)] = pm;
-        }
-        offl += totl;
-        offr += cnt - totl;
-        __syncthreads();
+      // partition into tmp (left block, then right block; the order inside a block does
+      // not matter), warp-aggregated reservations on two shared counters
+      if (t == 0) {
+        s_offl = 0;
+        s_offr = 0;
       }
+      __syncthreads();
+      {
+        const unsigned lt = (1u << (t & 31)) - 1u;
+        for (uint32_t cb = nb_; cb < ne_; cb += kTB) {
+          const uint32_t i = cb + t;
+          const bool ok = i < ne_;
+          uint32_t pm = 0;
+          bool isl = false;
+          if (ok) {
+            pm = perm[i];
+            isl = coord(u[pm], a) < xs;
+          }
+          const unsigned bl = __ballot_sync(0xffffffffu, ok && isl);
+          const unsigned br = __ballot_sync(0xffffffffu, ok && !isl);
+          uint32_t basel = 0, baser = 0;
+          if ((t & 31) == 0) {
+            basel = atomicAdd(&s_offl, (uint32_t)__popc(bl));
+            baser = atomicAdd(&s_offr, (uint32_t)__popc(br));
+          }
+          basel = __shfl_sync(0xffffffffu, basel, 0);
+          baser = __shfl_sync(0xffffffffu, baser, 0);
+          if (ok) {
+            if (isl) tmp[nb_ + basel + __popc(bl & lt)] = pm;
+            else tmp[nb_ + nleft + baser + __popc(br & lt)] = pm;
+          }
+        }
+      }
+      __syncthreads();
       for (uint32_t i = nb_ + t; i < ne_; i += kTB) perm[i] = tmp[i];
       __syncthreads();
       if (t == 0) {
@@ -557,13 +593,13 @@ vr_status run_background(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Aren
   void *scr = ar.take<char>(scan_scratch_bytes<uint32_t>(hmax + 1));
   if (!ar.ok()) return set_error(ctx, VR_ERR_WORKSPACE_TOO_SMALL, "workspace too small");
   if (H == 0) return VR_OK;
-  VR_TIMED(ctx, "halo_frame", s, k_halo_frame<<<(unsigned)H, kTB, 0, s>>>(g.hoff, g.hlabel, H, g.v, p->nsearch_min, halo_stats));
+  VR_TIMED(ctx, "halo_frame", s, k_halo_frame<<<(unsigned)H, kTB, 0, s>>>(g.hoff, g.hlabel, g.horder, H, g.v, p->nsearch_min, halo_stats));
   VR_LAUNCHED(ctx, "k_halo_frame");
   k_node_caps<<<grid_for(H + 1, 256), 256, 0, s>>>(g.hoff, H, p->nsearch_min, p->f_cell,
                                                    p->ncell_min, bg.nodeoff);
   VR_LAUNCHED(ctx, "k_node_caps");
   VR_CUDA(ctx, exclusive_scan<uint32_t>(bg.nodeoff, bg.nodeoff, H + 1, scr, s));
-  VR_TIMED(ctx, "cells_build", s, k_cells_build<<<(unsigned)H, kTB, 0, s>>>(g.hoff, bg.nodeoff, H, g.u, g.v, p->nsearch_min,
+  VR_TIMED(ctx, "cells_build", s, k_cells_build<<<(unsigned)H, kTB, 0, s>>>(g.hoff, g.horder, bg.nodeoff, H, g.u, g.v, p->nsearch_min,
                                            p->f_cell, p->ncell_min, p->split_rule, perm, tmp,
                                            bg.nodes, bg.mom, bg.leaf_of, halo_stats,
                                            ctx->d_status));

@@ -142,6 +142,7 @@ __device__ bool solve4(double M[4][4], const double *b, double *x) {
 }  // namespace
 
 __global__ void __launch_bounds__(kFT) k_ell_fit(const uint32_t *__restrict__ hoff,
+                                                 const uint32_t *__restrict__ horder,
                                                  const uint32_t *__restrict__ nodeoff, int64_t H,
                                                  const float4 *__restrict__ v,
                                                  const float *__restrict__ R, int nb_min,
@@ -154,8 +155,8 @@ __global__ void __launch_bounds__(kFT) k_ell_fit(const uint32_t *__restrict__ ho
   __shared__ int s_cnt[kMaxFitBins];
   __shared__ int s_n;
   __shared__ double s_par[8];
-  const int64_t h = blockIdx.x;
-  if (h >= H) return;
+  if ((int64_t)blockIdx.x >= H) return;
+  const int64_t h = horder[blockIdx.x];  // largest halos first
   if (nodeoff[h + 1] == nodeoff[h]) return;  // not searched
   const uint32_t hb = hoff[h], he = hoff[h + 1];
   const int nh = (int)(he - hb);
@@ -312,7 +313,7 @@ vr_status run_fit(vr_ctx *ctx, const HaloSeg &g, const Background &bg, const vr_
   if (g.H == 0) return VR_OK;
   if (p->fit_nbins_max > kMaxFitBins)
     return set_error(ctx, VR_ERR_INVALID_ARG, "fit_nbins_max above %d", kMaxFitBins);
-  VR_TIMED(ctx, "ell_fit", s, k_ell_fit<<<(unsigned)g.H, kFT, 0, s>>>(g.hoff, bg.nodeoff, g.H, g.v, R, p->fit_nbins_min,
+  VR_TIMED(ctx, "ell_fit", s, k_ell_fit<<<(unsigned)g.H, kFT, 0, s>>>(g.hoff, g.horder, bg.nodeoff, g.H, g.v, R, p->fit_nbins_min,
                                           p->fit_nbins_max, p->fit_iters, halo_stats, ell));
   VR_LAUNCHED(ctx, "k_ell_fit");
   return VR_OK;

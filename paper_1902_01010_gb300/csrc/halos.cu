@@ -157,6 +157,15 @@ __global__ void k_gather_morton(const uint32_t *__restrict__ perm, const int4 *_
   hid_out[m] = hkey_in[src];
 }
 
+// keys that sort halos by decreasing size
+__global__ void k_size_keys(const uint32_t *__restrict__ hoff, int64_t H, uint32_t *__restrict__ keys,
+                            uint32_t *__restrict__ vals) {
+  int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= H) return;
+  keys[h] = 0xffffffffu - (hoff[h + 1] - hoff[h]);
+  vals[h] = (uint32_t)h;
+}
+
 int bitlen(uint64_t x) {
   int b = 0;
   while (x) { ++b; x >>= 1; }
@@ -202,6 +211,7 @@ size_t halo_seg_bytes(int64_t n, int nmin) {
   int64_t hmax = n / (nmin > 0 ? nmin : 1) + 2;
   ar.take<uint32_t>(hmax + 1);  // hoff
   ar.take<uint32_t>(hmax);      // hlabel
+  ar.take<uint32_t>(hmax);      // horder
   ar.take<uint32_t>(n);         // hid
   ar.take<int4>(n);             // u
   ar.take<float4>(n);           // v
@@ -217,6 +227,7 @@ vr_status build_halos(vr_ctx *ctx, const int32_t *pos, const float *vel, int64_t
   int64_t hmax = n / (nmin > 0 ? nmin : 1) + 2;
   g.hoff = ar.take<uint32_t>(hmax + 1);
   g.hlabel = ar.take<uint32_t>(hmax);
+  g.horder = ar.take<uint32_t>(hmax);
   g.hid = ar.take<uint32_t>(n);
   g.u = ar.take<int4>(n);
   g.v = ar.take<float4>(n);
@@ -267,6 +278,12 @@ vr_status build_halos(vr_ctx *ctx, const int32_t *pos, const float *vel, int64_t
   uint32_t *perm = which ? B.mv1 : B.mv0;
   k_gather_morton<<<grid_for(NHP, T), T, 0, s>>>(perm, B.u_idx, idx, hkey, vel, NHP, g.u, g.v, g.hid);
   VR_LAUNCHED(ctx, "k_gather_morton");
+  // halo work order: decreasing size (the sort is stable, so equal sizes keep label order)
+  k_size_keys<<<grid_for(H, T), T, 0, s>>>(g.hoff, H, B.k0, B.v0);
+  VR_LAUNCHED(ctx, "k_size_keys");
+  VR_CUDA(ctx, radix_sort_pairs<uint32_t>(B.k0, B.v0, B.k1, B.v1, H, 0, 32, B.scr, s, &which));
+  VR_CUDA(ctx, cudaMemcpyAsync(g.horder, which ? B.v1 : B.v0, H * sizeof(uint32_t),
+                               cudaMemcpyDeviceToDevice, s));
   (void)nsmall;
   return VR_OK;
 }

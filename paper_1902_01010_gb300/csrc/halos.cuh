@@ -15,6 +15,7 @@ struct HaloSeg {
   int64_t nbig = 0;    // halos with more than nsmall members (host copy)
   uint32_t *hoff;      // [H+1] first slot of each halo
   uint32_t *hlabel;    // [H] halo label (minimum particle index)
+  uint32_t *horder;    // [H] halos by decreasing size (work order of per-halo kernels)
   uint32_t *hid;       // [NHP] halo of each slot
   int4 *u;             // [NHP] unwrapped position (x, y, z) and local index w
   float4 *v;           // [NHP] velocity (x, y, z) and particle index (w, as int bits)
