@@ -44,7 +44,7 @@ WORKLOADS = {
 SAMPLE_BOX = "m64"
 SAMPLE_DESC = ("64^3 box (262,144 particles) drawn by the same generator with the same "
                "parameters; full oracle pipeline (3D FOF, f_l, background R, fit, 6D links)")
-TIMED_KERNELS = ("velden_big", "fof_link", "link6", "cells_build", "ell_fit", "ratio",
+TIMED_KERNELS = ("velden_big", "fof_link", "link6", "cells_build", "cells_build_big", "ell_fit", "ratio",
                  "halo_frame", "velden_small")
 
 

@@ -207,7 +207,7 @@ vr_status vr_fof3d_noalloc(const int32_t *pos, int64_t n, int64_t link_d2, int32
  * (no counterpart in the paper: instrumentation of this library)
  * Per-kernel device timing with CUDA events recorded on the launching stream; off by
  * default. Kernel names: "fof_link", "velden_big", "velden_small", "halo_frame",
- * "cells_build", "ratio", "ell_fit", "link6". */
+ * "cells_build", "cells_build_big", "ratio", "ell_fit", "link6". */
 
 /* Enables (1) or disables (0) event timing of the named kernels for this context. */
 vr_status vr_timing_enable(vr_ctx *ctx, int enable);

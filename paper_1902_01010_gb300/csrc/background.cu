@@ -26,7 +26,10 @@ namespace vr {
 
 namespace {
 
-constexpr int kTB = 256;           // threads per tree-building CTA
+constexpr int kFrameT = 256;       // threads per halo-frame CTA
+constexpr int kSmallT = 256;       // threads per tree-building CTA, halos below kBigHalo
+constexpr int kBigT = 1024;        // threads per tree-building CTA, halos of kBigHalo or more
+constexpr int64_t kBigHalo = 65536;
 constexpr int kMaxBins = 162;      // floor((2^22)^(1/3)) + 1
 constexpr int kSmallNode = 1024;   // nodes up to this size find their median by counting
 
@@ -47,7 +50,7 @@ __device__ __forceinline__ int64_t icbrt_dev(int64_t n) {
 }
 
 // ---- block reductions (256 threads) ----
-template <class T, class Op>
+template <int NT, class T, class Op>
 __device__ __forceinline__ T block_reduce(T v, Op op, T *sbuf) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int o = 16; o; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -55,7 +58,7 @@ __device__ __forceinline__ T block_reduce(T v, Op op, T *sbuf) {
   if (lane == 0) sbuf[w] = v;
   __syncthreads();
   T r = sbuf[0];
-  for (int k = 1; k < kTB / 32; ++k) r = op(r, sbuf[k]);
+  for (int k = 1; k < NT / 32; ++k) r = op(r, sbuf[k]);
   __syncthreads();
   return r;
 }
@@ -71,34 +74,34 @@ __device__ __forceinline__ int coord(const int4 &p, int a) { return a == 0 ? p.x
 }  // namespace
 
 // Halo table row for every halo (searched or not): FP64 frame and sigma_host.
-__global__ void __launch_bounds__(kTB) k_halo_frame(const uint32_t *__restrict__ hoff,
+__global__ void __launch_bounds__(kFrameT) k_halo_frame(const uint32_t *__restrict__ hoff,
                                                     const uint32_t *__restrict__ hlabel,
                                                     const uint32_t *__restrict__ horder, int64_t H,
                                                     const float4 *__restrict__ v, int nsearch_min,
                                                     double *__restrict__ hs_out) {
-  __shared__ double sd[kTB / 32];
+  __shared__ double sd[kFrameT / 32];
   if ((int64_t)blockIdx.x >= H) return;
   const int64_t h = horder[blockIdx.x];  // largest halos first
   const uint32_t b = hoff[h], e = hoff[h + 1];
   const double nh = (double)(e - b);
   double s[3] = {0, 0, 0};
-  for (uint32_t m = b + threadIdx.x; m < e; m += kTB) {
+  for (uint32_t m = b + threadIdx.x; m < e; m += kFrameT) {
     float4 q = v[m];
     s[0] += (double)q.x;
     s[1] += (double)q.y;
     s[2] += (double)q.z;
   }
   double mean[3];
-  for (int k = 0; k < 3; ++k) mean[k] = block_reduce(s[k], AddD(), sd) / nh;
+  for (int k = 0; k < 3; ++k) mean[k] = block_reduce<kFrameT>(s[k], AddD(), sd) / nh;
   double c[6] = {0, 0, 0, 0, 0, 0};
-  for (uint32_t m = b + threadIdx.x; m < e; m += kTB) {
+  for (uint32_t m = b + threadIdx.x; m < e; m += kFrameT) {
     float4 q = v[m];
     double d0 = (double)q.x - mean[0], d1 = (double)q.y - mean[1], d2 = (double)q.z - mean[2];
     c[0] += d0 * d0; c[1] += d1 * d1; c[2] += d2 * d2;
     c[3] += d0 * d1; c[4] += d0 * d2; c[5] += d1 * d2;
   }
   double S[6];
-  for (int k = 0; k < 6; ++k) S[k] = block_reduce(c[k], AddD(), sd) / nh;
+  for (int k = 0; k < 6; ++k) S[k] = block_reduce<kFrameT>(c[k], AddD(), sd) / nh;
   if (threadIdx.x == 0) {
     double det = S[0] * (S[1] * S[2] - S[5] * S[5]) - S[3] * (S[3] * S[2] - S[5] * S[4]) +
                  S[4] * (S[3] * S[5] - S[1] * S[4]);
@@ -136,7 +139,8 @@ __global__ void k_node_caps(const uint32_t *__restrict__ hoff, int64_t H, int ns
   caps[h] = (uint32_t)(kNodeFactor * ((nh + nc) / (nc + 1)) + 16);
 }
 
-__global__ void __launch_bounds__(kTB) k_cells_build(
+template <int NT>
+__global__ void __launch_bounds__(NT) k_cells_build(
     const uint32_t *__restrict__ hoff, const uint32_t *__restrict__ horder,
     const uint32_t *__restrict__ nodeoff, int64_t H,
     const int4 *__restrict__ u, const float4 *__restrict__ v, int nsearch_min, double f_cell,
@@ -145,15 +149,15 @@ __global__ void __launch_bounds__(kTB) k_cells_build(
     double *__restrict__ hs_out, DevStatus *st) {
   __shared__ int s_hist[3][kMaxBins];
   __shared__ uint32_t s_dig[256];
-  __shared__ int s_ri[kTB / 32];
-  __shared__ long long s_rl[kTB / 32];
-  __shared__ double s_rd[kTB / 32];
+  __shared__ int s_ri[NT / 32];
+  __shared__ long long s_rl[NT / 32];
+  __shared__ double s_rd[NT / 32];
   __shared__ int s_order[3];
   __shared__ int s_norder;
   __shared__ unsigned long long s_prefix;
   __shared__ int s_rank;
   __shared__ int s_count;
-  __shared__ uint32_t s_scan[kTB];
+  __shared__ uint32_t s_scan[NT];
   __shared__ unsigned long long s_keys[kSmallNode];
   __shared__ uint32_t s_offl, s_offr;
   if ((int64_t)blockIdx.x >= H) return;
@@ -161,21 +165,22 @@ __global__ void __launch_bounds__(kTB) k_cells_build(
   const uint32_t hb = hoff[h], he = hoff[h + 1];
   const int64_t nh = he - hb;
   if (nh < nsearch_min) return;
+  if ((NT == kBigT) != (nh >= kBigHalo)) return;  // each size class has its own launch
   const int64_t ncell = ncell_of(nh, f_cell, ncell_min);
   const uint32_t base = nodeoff[h], cap = nodeoff[h + 1] - base;
   const int t = threadIdx.x;
-  for (uint32_t m = hb + t; m < he; m += kTB) perm[m] = m;
+  for (uint32_t m = hb + t; m < he; m += NT) perm[m] = m;
   // root region: [min, max + 1)
   {
     int mn[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff}, mx[3] = {-0x7fffffff, -0x7fffffff, -0x7fffffff};
-    for (uint32_t m = hb + t; m < he; m += kTB) {
+    for (uint32_t m = hb + t; m < he; m += NT) {
       int4 p = u[m];
       mn[0] = min(mn[0], p.x); mn[1] = min(mn[1], p.y); mn[2] = min(mn[2], p.z);
       mx[0] = max(mx[0], p.x); mx[1] = max(mx[1], p.y); mx[2] = max(mx[2], p.z);
     }
     for (int a = 0; a < 3; ++a) {
-      int lo = block_reduce(mn[a], MinOp(), s_ri);
-      int hi = block_reduce(mx[a], MaxOp(), s_ri);
+      int lo = block_reduce<NT>(mn[a], MinOp(), s_ri);
+      int hi = block_reduce<NT>(mx[a], MaxOp(), s_ri);
       if (t == 0) {
         nodes[base].lo[a] = lo;
         nodes[base].hi[a] = hi + 1;
@@ -201,20 +206,22 @@ __global__ void __launch_bounds__(kTB) k_cells_build(
     }
     // extent of the node's members per axis
     int mn[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff}, mx[3] = {-0x7fffffff, -0x7fffffff, -0x7fffffff};
-    for (uint32_t i = nb_ + t; i < ne_; i += kTB) {
+#pragma unroll 4
+    for (uint32_t i = nb_ + t; i < ne_; i += NT) {
       int4 p = u[perm[i]];
       mn[0] = min(mn[0], p.x); mn[1] = min(mn[1], p.y); mn[2] = min(mn[2], p.z);
       mx[0] = max(mx[0], p.x); mx[1] = max(mx[1], p.y); mx[2] = max(mx[2], p.z);
     }
     int amin[3], amax[3];
     for (int a = 0; a < 3; ++a) {
-      amin[a] = block_reduce(mn[a], MinOp(), s_ri);
-      amax[a] = block_reduce(mx[a], MaxOp(), s_ri);
+      amin[a] = block_reduce<NT>(mn[a], MinOp(), s_ri);
+      amax[a] = block_reduce<NT>(mx[a], MaxOp(), s_ri);
     }
     const int64_t nbins = max((int64_t)2, icbrt_dev(n));
-    for (int k = t; k < 3 * kMaxBins; k += kTB) (&s_hist[0][0])[k] = 0;
+    for (int k = t; k < 3 * kMaxBins; k += NT) (&s_hist[0][0])[k] = 0;
     __syncthreads();
-    for (uint32_t i = nb_ + t; i < ne_; i += kTB) {
+#pragma unroll 4
+    for (uint32_t i = nb_ + t; i < ne_; i += NT) {
       int4 p = u[perm[i]];
       for (int a = 0; a < 3; ++a) {
         if (amax[a] > amin[a]) {
@@ -230,7 +237,7 @@ __global__ void __launch_bounds__(kTB) k_cells_build(
     for (int a = 0; a < 3; ++a) {
       double part = 0.0;
       if (amax[a] > amin[a]) {
-        for (int b = t; b < nbins; b += kTB) {
+        for (int b = t; b < nbins; b += NT) {
           int c = s_hist[a][b];
           if (c > 0) {
             double f = (double)c / (double)n;
@@ -238,7 +245,7 @@ __global__ void __launch_bounds__(kTB) k_cells_build(
           }
         }
       }
-      Sa[a] = block_reduce(part, AddD(), s_rd);
+      Sa[a] = block_reduce<NT>(part, AddD(), s_rd);
     }
     if (t == 0) {
       double S[3];
@@ -274,10 +281,10 @@ __global__ void __launch_bounds__(kTB) k_cells_build(
       };
       if (n <= kSmallNode) {
         // small node: rank by counting, keys staged in shared memory
-        for (uint32_t i = nb_ + t; i < ne_; i += kTB) s_keys[i - nb_] = node_key(i);
+        for (uint32_t i = nb_ + t; i < ne_; i += NT) s_keys[i - nb_] = node_key(i);
         __syncthreads();
         const int target = (int)(n / 2);
-        for (int i = t; i < (int)n; i += kTB) {
+        for (int i = t; i < (int)n; i += NT) {
           const unsigned long long ki = s_keys[i];
           int below = 0;
           for (int j = 0; j < (int)n; ++j) below += s_keys[j] < ki ? 1 : 0;
@@ -298,34 +305,36 @@ __global__ void __launch_bounds__(kTB) k_cells_build(
         }
         __syncthreads();
         for (int d = ndig - 1; d >= 0; --d) {
-          s_dig[t] = 0;
+          if (t < 256) s_dig[t] = 0;
           __syncthreads();
           const int sh = 8 * d;
           const unsigned long long pre = s_prefix;
-          for (uint32_t i = nb_ + t; i < ne_; i += kTB) {
+#pragma unroll 4
+          for (uint32_t i = nb_ + t; i < ne_; i += NT) {
             unsigned long long key = node_key(i);
             unsigned long long hiK = (sh + 8 >= 64) ? 0ULL : (key >> (sh + 8));
             unsigned long long hiP = (sh + 8 >= 64) ? 0ULL : (pre >> (sh + 8));
             if (hiK == hiP) atomicAdd(&s_dig[(key >> sh) & 0xffu], 1u);
           }
           __syncthreads();
-          // exclusive scan of the 256 digit counts (thread t owns digit t): warp scans,
-          // then the 8 warp totals
-          const uint32_t c = s_dig[t];
+          // exclusive scan of the 256 digit counts (thread t < 256 owns digit t): warp
+          // scans, then the 8 warp totals
+          const uint32_t c = t < 256 ? s_dig[t] : 0u;
           uint32_t incl = c;
           for (int o = 1; o < 32; o <<= 1) {
             uint32_t x = __shfl_up_sync(0xffffffffu, incl, o);
             if ((t & 31) >= o) incl += x;
           }
-          if ((t & 31) == 31) s_scan[t >> 5] = incl;
+          if (t < 256 && (t & 31) == 31) s_scan[t >> 5] = incl;
           __syncthreads();
           uint32_t wbase = 0;
-          for (int w = 0; w < (t >> 5); ++w) wbase += s_scan[w];
+          if (t < 256)
+            for (int w = 0; w < (t >> 5); ++w) wbase += s_scan[w];
           incl += wbase;
           const uint32_t excl = incl - c;
           const int rk = s_rank;
           __syncthreads();
-          if ((int)excl <= rk && rk < (int)incl) {
+          if (t < 256 && (int)excl <= rk && rk < (int)incl) {
             s_prefix = pre | ((unsigned long long)t << sh);
             s_rank = rk - (int)excl;
           }
@@ -335,8 +344,9 @@ __global__ void __launch_bounds__(kTB) k_cells_build(
       const int xs = lo_a + (int)(s_prefix >> 22);
       // left = {x < xs}
       int cl = 0;
-      for (uint32_t i = nb_ + t; i < ne_; i += kTB) cl += coord(u[perm[i]], a) < xs ? 1 : 0;
-      const int nleft = block_reduce(cl, AddI(), s_ri);
+#pragma unroll 4
+      for (uint32_t i = nb_ + t; i < ne_; i += NT) cl += coord(u[perm[i]], a) < xs ? 1 : 0;
+      const int nleft = block_reduce<NT>(cl, AddI(), s_ri);
       if (nleft == 0) continue;  // left side empty: next axis
       // partition into tmp (left block, then right block; the order inside a block does
       // not matter), warp-aggregated reservations on two shared counters
@@ -347,7 +357,7 @@ __global__ void __launch_bounds__(kTB) k_cells_build(
       __syncthreads();
       {
         const unsigned lt = (1u << (t & 31)) - 1u;
-        for (uint32_t cb = nb_; cb < ne_; cb += kTB) {
+        for (uint32_t cb = nb_; cb < ne_; cb += NT) {
           const uint32_t i = cb + t;
           const bool ok = i < ne_;
           uint32_t pm = 0;
@@ -372,7 +382,8 @@ __global__ void __launch_bounds__(kTB) k_cells_build(
         }
       }
       __syncthreads();
-      for (uint32_t i = nb_ + t; i < ne_; i += kTB) perm[i] = tmp[i];
+#pragma unroll 4
+      for (uint32_t i = nb_ + t; i < ne_; i += NT) perm[i] = tmp[i];
       __syncthreads();
       if (t == 0) {
         int c0 = s_count;
@@ -416,7 +427,7 @@ __global__ void __launch_bounds__(kTB) k_cells_build(
     const double M = (double)(e - b);
     long long sx[3] = {0, 0, 0};
     double sv[3] = {0, 0, 0};
-    for (uint32_t i = b + t; i < e; i += kTB) {
+    for (uint32_t i = b + t; i < e; i += NT) {
       uint32_t m = perm[i];
       leaf_of[m] = base + cur;
       int4 p = u[m];
@@ -426,18 +437,18 @@ __global__ void __launch_bounds__(kTB) k_cells_build(
     }
     double xm[3], vm[3];
     for (int k = 0; k < 3; ++k) {
-      xm[k] = (double)block_reduce(sx[k], AddL(), s_rl) / M;
-      vm[k] = block_reduce(sv[k], AddD(), s_rd) / M;
+      xm[k] = (double)block_reduce<NT>(sx[k], AddL(), s_rl) / M;
+      vm[k] = block_reduce<NT>(sv[k], AddD(), s_rd) / M;
     }
     double c[6] = {0, 0, 0, 0, 0, 0};
-    for (uint32_t i = b + t; i < e; i += kTB) {
+    for (uint32_t i = b + t; i < e; i += NT) {
       float4 q = v[perm[i]];
       double d0 = (double)q.x - vm[0], d1 = (double)q.y - vm[1], d2 = (double)q.z - vm[2];
       c[0] += d0 * d0; c[1] += d1 * d1; c[2] += d2 * d2;
       c[3] += d0 * d1; c[4] += d0 * d2; c[5] += d1 * d2;
     }
     double S6[6];
-    for (int k = 0; k < 6; ++k) S6[k] = block_reduce(c[k], AddD(), s_rd) / M;
+    for (int k = 0; k < 6; ++k) S6[k] = block_reduce<NT>(c[k], AddD(), s_rd) / M;
     if (t == 0) {
       double *o = mom + 13 * (int64_t)(base + cur);
       o[0] = M;
@@ -593,16 +604,28 @@ vr_status run_background(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Aren
   void *scr = ar.take<char>(scan_scratch_bytes<uint32_t>(hmax + 1));
   if (!ar.ok()) return set_error(ctx, VR_ERR_WORKSPACE_TOO_SMALL, "workspace too small");
   if (H == 0) return VR_OK;
-  VR_TIMED(ctx, "halo_frame", s, k_halo_frame<<<(unsigned)H, kTB, 0, s>>>(g.hoff, g.hlabel, g.horder, H, g.v, p->nsearch_min, halo_stats));
+  VR_TIMED(ctx, "halo_frame", s, k_halo_frame<<<(unsigned)H, kFrameT, 0, s>>>(g.hoff, g.hlabel, g.horder, H, g.v, p->nsearch_min, halo_stats));
   VR_LAUNCHED(ctx, "k_halo_frame");
   k_node_caps<<<grid_for(H + 1, 256), 256, 0, s>>>(g.hoff, H, p->nsearch_min, p->f_cell,
                                                    p->ncell_min, bg.nodeoff);
   VR_LAUNCHED(ctx, "k_node_caps");
   VR_CUDA(ctx, exclusive_scan<uint32_t>(bg.nodeoff, bg.nodeoff, H + 1, scr, s));
-  VR_TIMED(ctx, "cells_build", s, k_cells_build<<<(unsigned)H, kTB, 0, s>>>(g.hoff, g.horder, bg.nodeoff, H, g.u, g.v, p->nsearch_min,
-                                           p->f_cell, p->ncell_min, p->split_rule, perm, tmp,
-                                           bg.nodes, bg.mom, bg.leaf_of, halo_stats,
-                                           ctx->d_status));
+  // Halos of kBigHalo members or more (the first entries of the size order) run with
+  // 1024-thread CTAs on the context's side stream while all other halos run with
+  // 256-thread CTAs on the caller's stream; the two launches overlap.
+  const int64_t nbig_max = g.NHP / kBigHalo + 1;
+  const unsigned big_grid = (unsigned)(nbig_max < H ? nbig_max : H);
+  VR_CUDA(ctx, cudaEventRecord(ctx->ev_fork, s));
+  VR_CUDA(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+  VR_TIMED(ctx, "cells_build_big", ctx->side, k_cells_build<kBigT><<<big_grid, kBigT, 0, ctx->side>>>(
+      g.hoff, g.horder, bg.nodeoff, H, g.u, g.v, p->nsearch_min, p->f_cell, p->ncell_min,
+      p->split_rule, perm, tmp, bg.nodes, bg.mom, bg.leaf_of, halo_stats, ctx->d_status));
+  VR_LAUNCHED(ctx, "k_cells_build<big>");
+  VR_TIMED(ctx, "cells_build", s, k_cells_build<kSmallT><<<(unsigned)H, kSmallT, 0, s>>>(
+      g.hoff, g.horder, bg.nodeoff, H, g.u, g.v, p->nsearch_min, p->f_cell, p->ncell_min,
+      p->split_rule, perm, tmp, bg.nodes, bg.mom, bg.leaf_of, halo_stats, ctx->d_status));
+  VR_CUDA(ctx, cudaEventRecord(ctx->ev_join, ctx->side));
+  VR_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev_join, 0));
   VR_LAUNCHED(ctx, "k_cells_build");
   unsigned long long *ndeg = (unsigned long long *)&ctx->d_status->info[0];
   VR_TIMED(ctx, "ratio", s, k_ratio<<<grid_for(g.NHP, 256), 256, 0, s>>>(g.hid, bg.nodeoff, g.NHP, g.u, g.v, f_l, bg.nodes,

@@ -186,7 +186,10 @@ vr_status vr_create(vr_ctx **out, int device) {
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
   if (cudaMalloc(&c->d_status, sizeof(DevStatus)) != cudaSuccess ||
       cudaMallocHost(&c->h_pinned, 64 * sizeof(long long)) != cudaSuccess ||
-      cudaMemset(c->d_status, 0, sizeof(DevStatus)) != cudaSuccess) {
+      cudaMemset(c->d_status, 0, sizeof(DevStatus)) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
     vr_destroy(c);
     return VR_ERR_CUDA;
   }
@@ -197,6 +200,9 @@ vr_status vr_create(vr_ctx **out, int device) {
 void vr_destroy(vr_ctx *ctx) {
   if (!ctx) return;
   timers_free(ctx->timers);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
   free(ctx);

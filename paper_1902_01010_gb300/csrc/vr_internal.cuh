@@ -36,6 +36,8 @@ struct vr_ctx {
   vr::DevStatus *d_status;  // device
   long long *h_pinned;      // pinned host staging (64 entries)
   vr::Timers *timers;       // NULL unless timing is enabled
+  cudaStream_t side;        // second stream for work that overlaps the caller's stream
+  cudaEvent_t ev_fork, ev_join;
 };
 
 namespace vr {
