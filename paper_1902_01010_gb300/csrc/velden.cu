@@ -31,8 +31,8 @@ namespace vr {
 namespace {
 
 constexpr int kNVMax = 64;
-constexpr int kBins = 32;
-constexpr int kBuf = 16;
+constexpr int kBins = 64;
+constexpr int kBuf = 32;
 constexpr int kWarps = 4;        // warps per block
 
 // Optional instrumentation (compile with -DVR_VELDEN_STATS): warp-level counts of the
@@ -54,10 +54,7 @@ struct WarpSmem {
   float4 sv[32];
   union {
     uint16_t hist[kBins][32];
-    struct {
-      u64 bkey[kBuf][32];
-      float bdv[kBuf][32];
-    };
+    uint32_t bslot[kBuf][32];  // member slots of the keys in the final bin
   };
   float top[NVM][32];
 };
@@ -302,7 +299,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
       }
     }
     for (int cb = 0; cb < kBins; ++cb) sm.hist[cb][lane] = 0;
-    int sh0 = bitlen64((unsigned long long)wmax) - 5;  // 32 bins over [0, 2^bitlen)
+    int sh0 = bitlen64((unsigned long long)wmax) - 6;  // 64 bins over [0, 2^bitlen)
     if (sh0 < 0) sh0 = 0;
     for (int c = 0; c < W; c += 32) {
       const int cnt = min(32, W - c);
@@ -355,17 +352,21 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
       }
     }
   };
-  // 2. histogram passes over the exact keys (d^2 << 22 | local index)
-  u64 klo = 0;
-  int sh = bitlen64(((u64)(r2 + 1) << 22) - 1) - 5;
+  // 2. histogram passes over the exact keys (d^2 << 22 | local index). The first level
+  //    spreads its bins over [r2/4, r2] only (the N_se-th key lies near the bound) and
+  //    counts the keys below in one register; later levels split the chosen bin.
+  u64 klo = (u64)(r2 >> 2) << 22;
+  int sh = bitlen64((((u64)(r2 + 1)) << 22) - klo - 1) - 6;
   if (sh < 0) sh = 0;
   int need = nse_eff;
   bool settled = !valid;
   u64 fin_lo = 0, fin_hi = 0;
   int need_in = 0;
   long long rcur = r2;  // per-lane bound on d^2 of keys still of interest
+  bool focus = true;    // this lane's current level is the focused first level
   for (int level = 0; level < 16; ++level) {
     pass_id = level < 5 ? 1 + level : 5;
+    int below = 0;
     if (!settled)
       for (int c = 0; c < kBins; ++c) sm.hist[c][lane] = 0;
     const long long rmax2 = warp_max(settled ? -1 : rcur);
@@ -387,6 +388,8 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
               if (key >= klo) {
                 u64 rel = (key - klo) >> sh;
                 if (rel < kBins) sm.hist[rel][lane]++;
+              } else if (focus) {
+                ++below;
               }
             }
           }
@@ -394,27 +397,40 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
       }
     });
     if (!settled) {
-      int cum = 0, bs = kBins - 1;
-      for (int c = 0; c < kBins; ++c) {
-        int hc = sm.hist[c][lane];
-        if (cum + hc >= need) {
-          bs = c;
-          break;
-        }
-        cum += hc;
-      }
-      int hc = sm.hist[bs][lane];
-      if (hc <= kBuf || sh == 0) {
-        fin_lo = klo + ((u64)bs << sh);
-        fin_hi = fin_lo + ((u64)1 << sh);
-        need_in = need - cum;
-        settled = true;
-      } else {
-        klo += (u64)bs << sh;
-        need -= cum;
-        const long long top_d = (long long)((klo + ((u64)1 << sh) - 1) >> 22);
+      if (focus && below >= need) {
+        // the N_se-th key lies below the focused range: bin [0, klo) next
+        const u64 hi = klo;
+        klo = 0;
+        sh = bitlen64(hi - 1) - 6;
+        if (sh < 0) sh = 0;
+        const long long top_d = (long long)((hi - 1) >> 22);
         rcur = top_d < rcur ? top_d : rcur;
-        sh = sh >= 5 ? sh - 5 : 0;
+        focus = false;
+      } else {
+        if (focus) need -= below;  // every key below the focused range is in
+        focus = false;
+        int cum = 0, bs = kBins - 1;
+        for (int c = 0; c < kBins; ++c) {
+          int hc = sm.hist[c][lane];
+          if (cum + hc >= need) {
+            bs = c;
+            break;
+          }
+          cum += hc;
+        }
+        int hc = sm.hist[bs][lane];
+        if (hc <= kBuf || sh == 0) {
+          fin_lo = klo + ((u64)bs << sh);
+          fin_hi = fin_lo + ((u64)1 << sh);
+          need_in = need - cum;
+          settled = true;
+        } else {
+          klo += (u64)bs << sh;
+          need -= cum;
+          const long long top_d = (long long)((klo + ((u64)1 << sh) - 1) >> 22);
+          rcur = top_d < rcur ? top_d : rcur;
+          sh = sh >= 6 ? sh - 6 : 0;
+        }
       }
     }
     if (__all_sync(FULL, settled)) break;
@@ -449,8 +465,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
             if (key < fin_lo) {
               top_insert(top, lane, tv, nv_eff, dv2f(sm.sv[t], vq));
             } else if (key < fin_hi && nbuf < kBuf) {
-              sm.bkey[nbuf][lane] = key;
-              sm.bdv[nbuf][lane] = dv2f(sm.sv[t], vq);
+              sm.bslot[nbuf][lane] = s0 + (uint32_t)t;
               ++nbuf;
             }
           }
@@ -459,20 +474,22 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
     }
   });
   if (!valid) return;
-  // the need_in smallest keys of the final bin
+  // the need_in smallest keys of the final bin (keys recomputed from the buffered slots)
+  u64 last = 0;
   for (int r = 0; r < need_in; ++r) {
     int best = -1;
     u64 bk = ~0ULL;
     for (int e = 0; e < nbuf; ++e) {
-      u64 x = sm.bkey[e][lane];
-      if (x < bk) {
+      const int4 pe = u[sm.bslot[e][lane]];
+      const u64 x = ((u64)d2i(q, pe) << 22) | (u64)pe.w;
+      if ((r == 0 || x > last) && x < bk) {
         bk = x;
         best = e;
       }
     }
     if (best < 0) break;
-    sm.bkey[best][lane] = ~0ULL;
-    top_insert(top, lane, tv, nv_eff, sm.bdv[best][lane]);
+    last = bk;
+    top_insert(top, lane, tv, nv_eff, dv2f(v[sm.bslot[best][lane]], vq));
   }
   f_l[__float_as_int(vq.w)] = top_density(top, lane, tv, nse_eff);
 }
