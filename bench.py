@@ -131,6 +131,11 @@ def measured_peaks():
 # selection of N_se out of the candidates and N_v out of N_se (one compare each) + the
 # Epanechnikov sum over N_v (3 ops): 256*8 + 256*8 + 256 + 256 + 32*3 = 4,704 ALU ops.
 VELDEN_OPS_PER_QUERY = 256 * 8 + 256 * 8 + 256 + 256 + 32 * 3
+# DRAM bytes per query particle of k_velden_big from one ncu capture of the 160^3 box
+# (41.6 MB over 1,183,473 queries; profiles/k_velden_big_160cubed.md). The kernel's DRAM
+# traffic grows with the number of queries, so a full launch is this times its queries.
+# Set to None whenever the kernel changes and the capture has not been redone.
+VELDEN_DRAM_BYTES_PER_QUERY = 41.572352e6 / 1183473
 SMS, LANES_PER_SM = 152, 128
 
 
@@ -260,8 +265,10 @@ def run_ours(args):
         achieved = ops / (per_launch_ms / 1e3) / 1e12
         sm_mhz = peaks.get("sm_max_mhz", 2070.0)
         peak = alu_peak_tops(sm_mhz)
+        traffic = (VELDEN_DRAM_BYTES_PER_QUERY * nq_big if VELDEN_DRAM_BYTES_PER_QUERY else None)
         roof = {"kernel": "k_velden_big", "bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "Tops/s", "frac": achieved / peak, "traffic": None,
+                "unit": "Tops/s", "frac": achieved / peak, "traffic": traffic,
+                "traffic_source": "ncu dram bytes per query on the 160^3 box x queries of this launch",
                 "peak_source": f"152 SMs x 128 lanes x {sm_mhz:.0f} MHz (sm_max_mhz of {how} peaks)",
                 "algorithmic": f"{VELDEN_OPS_PER_QUERY} ops x {int(nq_big)} query particles",
                 "launch_ms": per_launch_ms}
