@@ -144,6 +144,22 @@ def alu_peak_tops(sm_mhz):
     return SMS * LANES_PER_SM * sm_mhz * 1e6 / 1e12
 
 
+def reduce_over_ranks(ms, n_local, device=None):
+    """(slowest rank's time, all ranks' particles) across the process group (identity
+    without one). Replicas share nothing but this reduction."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms), float(n_local)
+    dev = device if device is not None else torch.device("cpu")
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(n_local)], dtype=torch.float64, device=dev)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(c.item())
+
+
 # ------------------------------------------------------------------------- ours
 def run_ours(args):
     import numpy as np
@@ -219,16 +235,13 @@ def run_ours(args):
         kern[nm] = (t.value, c.value)
     L.vr_timing_enable(ctx.h, 0)
     ctx.sync()
-    ms_max = ms
+    ms_max, n_all = reduce_over_ranks(ms, box.n, dev)
     if ws > 1:
         import torch.distributed as dist
 
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_max = float(tt.item())
         dist.barrier()
     ms_per_step = ms_max / args.steps
-    value = ws * box.n / (ms_per_step / 1e3)
+    value = n_all / (ms_per_step / 1e3)
 
     # ---- end to end through the public API with host buffers
     e2e = None
