@@ -3,13 +3,18 @@
 + skew-Gaussian fit + 6D outlier linking) on a synthetic 512^3 clustered box, one GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload c512] [--form plain|batched] [--no-cpu-baseline]
+                    [--workload c512] [--form batched|plain] [--plain-steps P]
+                    [--no-cpu-baseline]
 
 One step = vr_fof3d + vr_find_substructure over the whole box, inputs resident in HBM
 (3.2 GB of positions and velocities, far above the 129 MB L2, so no flush is needed
 between steps). Under torchrun (N > 1) every rank runs an independent replica on its own
 box (weak scaling, no collective on the data path); `value` is all ranks' particles over
 the slowest rank's time. Rank 0 prints one JSON line.
+
+The headline runs the batched form (each stage one launch over all halos); the same
+inputs are then timed in the plain form (each stage launched once per halo) and reported
+under "plain_form".
 
 --impl reference times the FP64 C oracle (the path's reference implementation) on the
 host cores, one step = the oracle pipeline over a bounded sample of the workload (a 64^3
@@ -264,6 +269,35 @@ def run_ours(args):
                "h2d_bytes_per_step": int(hpos.numel() * 4 + hvel.numel() * 4),
                "d2h_bytes_per_step": int(hl3.numel() * 4 + hl6.numel() * 4)}
 
+    # ---- the other launch form on the same inputs: one launch per halo and stage
+    plain = None
+    if batched and args.plain_steps > 0:
+        def step_plain():
+            ctx.fof3d(pos, box.link_d2, label=lab)
+            ctx.find_substructure(pos, vel, lab, box.lx_sub, 1.0, P, batched=0, out=out)
+
+        # no separate warm-up: every kernel and buffer was already used by the batched steps
+        ctx.sync()
+        if ws > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        l0 = L.vr_launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.plain_steps):
+            step_plain()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        pl_launch = L.vr_launch_count() - l0
+        pms, pn = reduce_over_ranks(e0.elapsed_time(e1), box.n, dev)
+        pms /= args.plain_steps
+        plain = {"value": pn / (pms / 1e3), "unit": "particles/s", "ms_per_step": pms,
+                 "steps": args.plain_steps, "warmup": "the batched steps (same kernels and buffers)",
+                 "gpu_launches_per_step": int(pl_launch // args.plain_steps),
+                 "batched_speedup": pms / ms_per_step}
+
     if rank != 0:
         return
     # ---- roofline of the dominant kernel (device time inside the timed region)
@@ -312,6 +346,7 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clk,
         "kernel_share_of_step": shares,
+        "plain_form": plain,
     }
     print(json.dumps(line), flush=True)
 
@@ -366,7 +401,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c512", choices=sorted(WORKLOADS))
-    ap.add_argument("--form", default="plain", choices=["plain", "batched"])
+    ap.add_argument("--form", default="batched", choices=["plain", "batched"],
+                    help="launch form of the headline number (batched: one launch per stage)")
+    ap.add_argument("--plain-steps", type=int, default=1,
+                    help="timed steps of the plain form (one launch per halo and stage) "
+                         "reported beside a batched headline; 0 skips it")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -172,9 +172,10 @@ vr_status vr_fof6d(vr_ctx *ctx, const int32_t *pos, const float *vel, const floa
 /* The substructure search of Fig. 2 (first pass) for every halo: vr_velden, then
  * vr_outlier_ratio, then the per-halo linking lengths lx2 = lx_sub^2 and
  * lv2 = (alpha_lv sigma_host)^2, then vr_fof6d on the outliers. Outputs as in those
- * calls; halo_stats gets LX2/LV2 filled in. `batched` selects the launch form:
- * 0 = one launch per stage over all halos with host-side sizing; 1 = same kernels
- * replayed from a captured CUDA graph (sizes kept on the device). */
+ * calls; halo_stats gets LX2/LV2 filled in. `batched` selects the launch form, with
+ * identical results: 1 = batched, each stage is one launch over all halos; 0 = plain,
+ * each stage is launched once per halo that has work in it (halo offsets are read back
+ * to the host once). Any other value returns VR_ERR_INVALID_ARG. */
 vr_status vr_find_substructure(vr_ctx *ctx, const int32_t *pos, const float *vel, int64_t n,
                                const int32_t *label, double lx_sub, double alpha_lv,
                                const vr_params *p, int batched, float *f_l, float *R,

@@ -18,6 +18,8 @@
 // along that axis, skipped outside the root region and counted once.
 #include <math.h>
 
+#include <vector>
+
 #include "halos.cuh"
 #include "vr_workspace.h"
 #include "background.cuh"
@@ -76,12 +78,12 @@ __device__ __forceinline__ int coord(const int4 &p, int a) { return a == 0 ? p.x
 // Halo table row for every halo (searched or not): FP64 frame and sigma_host.
 __global__ void __launch_bounds__(kFrameT) k_halo_frame(const uint32_t *__restrict__ hoff,
                                                     const uint32_t *__restrict__ hlabel,
-                                                    const uint32_t *__restrict__ horder, int64_t H,
-                                                    const float4 *__restrict__ v, int nsearch_min,
-                                                    double *__restrict__ hs_out) {
+                                                    const uint32_t *__restrict__ horder, int64_t first,
+                                                    int64_t last, const float4 *__restrict__ v,
+                                                    int nsearch_min, double *__restrict__ hs_out) {
   __shared__ double sd[kFrameT / 32];
-  if ((int64_t)blockIdx.x >= H) return;
-  const int64_t h = horder[blockIdx.x];  // largest halos first
+  if (first + (int64_t)blockIdx.x >= last) return;
+  const int64_t h = horder[first + blockIdx.x];  // largest halos first
   const uint32_t b = hoff[h], e = hoff[h + 1];
   const double nh = (double)(e - b);
   double s[3] = {0, 0, 0};
@@ -142,7 +144,7 @@ __global__ void k_node_caps(const uint32_t *__restrict__ hoff, int64_t H, int ns
 template <int NT>
 __global__ void __launch_bounds__(NT) k_cells_build(
     const uint32_t *__restrict__ hoff, const uint32_t *__restrict__ horder,
-    const uint32_t *__restrict__ nodeoff, int64_t H,
+    const uint32_t *__restrict__ nodeoff, int64_t first, int64_t last,
     const int4 *__restrict__ u, const float4 *__restrict__ v, int nsearch_min, double f_cell,
     int ncell_min, int split_rule, uint32_t *__restrict__ perm, uint32_t *__restrict__ tmp,
     CellNode *__restrict__ nodes, double *__restrict__ mom, uint32_t *__restrict__ leaf_of,
@@ -160,8 +162,8 @@ __global__ void __launch_bounds__(NT) k_cells_build(
   __shared__ uint32_t s_scan[NT];
   __shared__ unsigned long long s_keys[kSmallNode];
   __shared__ uint32_t s_offl, s_offr;
-  if ((int64_t)blockIdx.x >= H) return;
-  const int64_t h = horder[blockIdx.x];  // largest halos first
+  if (first + (int64_t)blockIdx.x >= last) return;
+  const int64_t h = horder[first + blockIdx.x];  // largest halos first
   const uint32_t hb = hoff[h], he = hoff[h + 1];
   const int64_t nh = he - hb;
   if (nh < nsearch_min) return;
@@ -491,12 +493,12 @@ __device__ __forceinline__ bool chol3(const double *s, double *L) {
 }
 
 __global__ void k_ratio(const uint32_t *__restrict__ hid, const uint32_t *__restrict__ nodeoff,
-                        int64_t nhp, const int4 *__restrict__ u, const float4 *__restrict__ v,
+                        int64_t m0, int64_t m1, const int4 *__restrict__ u, const float4 *__restrict__ v,
                         const float *__restrict__ f_l, const CellNode *__restrict__ nodes,
                         const double *__restrict__ mom, const uint32_t *__restrict__ leaf_of,
                         float *__restrict__ R, unsigned long long *__restrict__ ndegen) {
-  int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= nhp) return;
+  int64_t m = m0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // members [m0, m1)
+  if (m >= m1) return;
   const uint32_t h = hid[m];
   const uint32_t base = nodeoff[h];
   if (nodeoff[h + 1] == base) return;  // halo not searched
@@ -590,7 +592,7 @@ int64_t max_nodes(int64_t n, const vr_params *p) {
 
 vr_status run_background(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Arena &ar,
                          const float *f_l, float *R, double *halo_stats, Background *out,
-                         cudaStream_t s) {
+                         cudaStream_t s, const uint32_t *hoff_host) {
   const int64_t H = g.H;
   int64_t hmax = g.n / (p->nmin > 0 ? p->nmin : 1) + 2;
   Background &bg = *out;
@@ -604,12 +606,55 @@ vr_status run_background(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Aren
   void *scr = ar.take<char>(scan_scratch_bytes<uint32_t>(hmax + 1));
   if (!ar.ok()) return set_error(ctx, VR_ERR_WORKSPACE_TOO_SMALL, "workspace too small");
   if (H == 0) return VR_OK;
-  VR_TIMED(ctx, "halo_frame", s, k_halo_frame<<<(unsigned)H, kFrameT, 0, s>>>(g.hoff, g.hlabel, g.horder, H, g.v, p->nsearch_min, halo_stats));
-  VR_LAUNCHED(ctx, "k_halo_frame");
+  if (hoff_host) {
+    for (int64_t i = 0; i < H; ++i) {
+      k_halo_frame<<<1, kFrameT, 0, s>>>(g.hoff, g.hlabel, g.horder, i, i + 1, g.v, p->nsearch_min,
+                                         halo_stats);
+      VR_LAUNCHED(ctx, "k_halo_frame");
+    }
+  } else {
+    VR_TIMED(ctx, "halo_frame", s, k_halo_frame<<<(unsigned)H, kFrameT, 0, s>>>(
+        g.hoff, g.hlabel, g.horder, 0, H, g.v, p->nsearch_min, halo_stats));
+    VR_LAUNCHED(ctx, "k_halo_frame");
+  }
   k_node_caps<<<grid_for(H + 1, 256), 256, 0, s>>>(g.hoff, H, p->nsearch_min, p->f_cell,
                                                    p->ncell_min, bg.nodeoff);
   VR_LAUNCHED(ctx, "k_node_caps");
   VR_CUDA(ctx, exclusive_scan<uint32_t>(bg.nodeoff, bg.nodeoff, H + 1, scr, s));
+  auto build = [&](bool bigc, cudaStream_t st, int64_t a, int64_t z, unsigned grid) {
+    if (bigc)
+      k_cells_build<kBigT><<<grid, kBigT, 0, st>>>(g.hoff, g.horder, bg.nodeoff, a, z, g.u, g.v,
+                                                   p->nsearch_min, p->f_cell, p->ncell_min,
+                                                   p->split_rule, perm, tmp, bg.nodes, bg.mom,
+                                                   bg.leaf_of, halo_stats, ctx->d_status);
+    else
+      k_cells_build<kSmallT><<<grid, kSmallT, 0, st>>>(g.hoff, g.horder, bg.nodeoff, a, z, g.u,
+                                                       g.v, p->nsearch_min, p->f_cell,
+                                                       p->ncell_min, p->split_rule, perm, tmp,
+                                                       bg.nodes, bg.mom, bg.leaf_of, halo_stats,
+                                                       ctx->d_status);
+  };
+  unsigned long long *ndeg = (unsigned long long *)&ctx->d_status->info[0];
+  if (hoff_host) {
+    // one launch per searched halo, in the size order, with the CTA size of its class
+    std::vector<uint32_t> ord(H);
+    VR_CUDA(ctx, cudaMemcpyAsync(ord.data(), g.horder, H * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    VR_CUDA(ctx, cudaStreamSynchronize(s));
+    for (int64_t i = 0; i < H; ++i) {
+      const int64_t nh = hoff_host[ord[i] + 1] - hoff_host[ord[i]];
+      if (nh < p->nsearch_min) continue;
+      build(nh >= kBigHalo, s, i, i + 1, 1);
+      VR_LAUNCHED(ctx, nh >= kBigHalo ? "k_cells_build<big>" : "k_cells_build");
+    }
+    for (int64_t h = 0; h < H; ++h) {
+      const int64_t a = hoff_host[h], z = hoff_host[h + 1];
+      if (z - a < p->nsearch_min) continue;
+      k_ratio<<<grid_for(z - a, 256), 256, 0, s>>>(g.hid, bg.nodeoff, a, z, g.u, g.v, f_l, bg.nodes,
+                                                  bg.mom, bg.leaf_of, R, ndeg);
+      VR_LAUNCHED(ctx, "k_ratio");
+    }
+    return VR_OK;
+  }
   // Halos of kBigHalo members or more (the first entries of the size order) run with
   // 1024-thread CTAs on the context's side stream while all other halos run with
   // 256-thread CTAs on the caller's stream; the two launches overlap.
@@ -617,18 +662,13 @@ vr_status run_background(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Aren
   const unsigned big_grid = (unsigned)(nbig_max < H ? nbig_max : H);
   VR_CUDA(ctx, cudaEventRecord(ctx->ev_fork, s));
   VR_CUDA(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
-  VR_TIMED(ctx, "cells_build_big", ctx->side, k_cells_build<kBigT><<<big_grid, kBigT, 0, ctx->side>>>(
-      g.hoff, g.horder, bg.nodeoff, H, g.u, g.v, p->nsearch_min, p->f_cell, p->ncell_min,
-      p->split_rule, perm, tmp, bg.nodes, bg.mom, bg.leaf_of, halo_stats, ctx->d_status));
+  VR_TIMED(ctx, "cells_build_big", ctx->side, build(true, ctx->side, 0, H, big_grid));
   VR_LAUNCHED(ctx, "k_cells_build<big>");
-  VR_TIMED(ctx, "cells_build", s, k_cells_build<kSmallT><<<(unsigned)H, kSmallT, 0, s>>>(
-      g.hoff, g.horder, bg.nodeoff, H, g.u, g.v, p->nsearch_min, p->f_cell, p->ncell_min,
-      p->split_rule, perm, tmp, bg.nodes, bg.mom, bg.leaf_of, halo_stats, ctx->d_status));
+  VR_TIMED(ctx, "cells_build", s, build(false, s, 0, H, (unsigned)H));
+  VR_LAUNCHED(ctx, "k_cells_build");
   VR_CUDA(ctx, cudaEventRecord(ctx->ev_join, ctx->side));
   VR_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev_join, 0));
-  VR_LAUNCHED(ctx, "k_cells_build");
-  unsigned long long *ndeg = (unsigned long long *)&ctx->d_status->info[0];
-  VR_TIMED(ctx, "ratio", s, k_ratio<<<grid_for(g.NHP, 256), 256, 0, s>>>(g.hid, bg.nodeoff, g.NHP, g.u, g.v, f_l, bg.nodes,
+  VR_TIMED(ctx, "ratio", s, k_ratio<<<grid_for(g.NHP, 256), 256, 0, s>>>(g.hid, bg.nodeoff, 0, g.NHP, g.u, g.v, f_l, bg.nodes,
                                                bg.mom, bg.leaf_of, R, ndeg));
   VR_LAUNCHED(ctx, "k_ratio");
   return VR_OK;

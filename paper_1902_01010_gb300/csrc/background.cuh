@@ -28,5 +28,5 @@ int64_t max_nodes(int64_t n, const vr_params *p);
 size_t background_bytes(int64_t n, const vr_params *p);
 vr_status run_background(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Arena &ar,
                          const float *f_l, float *R, double *halo_stats, Background *out,
-                         cudaStream_t s);
+                         cudaStream_t s, const uint32_t *hoff_host = nullptr);
 }  // namespace vr

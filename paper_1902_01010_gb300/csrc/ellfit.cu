@@ -13,6 +13,8 @@
 //    with warp 0 spreading the bins over its lanes.
 #include <math.h>
 
+#include <vector>
+
 #include "halos.cuh"
 #include "vr_workspace.h"
 #include "background.cuh"
@@ -143,7 +145,8 @@ __device__ bool solve4(double M[4][4], const double *b, double *x) {
 
 __global__ void __launch_bounds__(kFT) k_ell_fit(const uint32_t *__restrict__ hoff,
                                                  const uint32_t *__restrict__ horder,
-                                                 const uint32_t *__restrict__ nodeoff, int64_t H,
+                                                 const uint32_t *__restrict__ nodeoff,
+                                                 int64_t first, int64_t last,
                                                  const float4 *__restrict__ v,
                                                  const float *__restrict__ R, int nb_min,
                                                  int nb_max, int iters, double *__restrict__ hs,
@@ -155,8 +158,8 @@ __global__ void __launch_bounds__(kFT) k_ell_fit(const uint32_t *__restrict__ ho
   __shared__ int s_cnt[kMaxFitBins];
   __shared__ int s_n;
   __shared__ double s_par[8];
-  if ((int64_t)blockIdx.x >= H) return;
-  const int64_t h = horder[blockIdx.x];  // largest halos first
+  if (first + (int64_t)blockIdx.x >= last) return;
+  const int64_t h = horder[first + blockIdx.x];  // largest halos first
   if (nodeoff[h + 1] == nodeoff[h]) return;  // not searched
   const uint32_t hb = hoff[h], he = hoff[h + 1];
   const int nh = (int)(he - hb);
@@ -309,12 +312,25 @@ __global__ void __launch_bounds__(kFT) k_ell_fit(const uint32_t *__restrict__ ho
 }
 
 vr_status run_fit(vr_ctx *ctx, const HaloSeg &g, const Background &bg, const vr_params *p,
-                  const float *R, double *halo_stats, float *ell, cudaStream_t s) {
+                  const float *R, double *halo_stats, float *ell, cudaStream_t s, const uint32_t *hoff_host) {
   if (g.H == 0) return VR_OK;
   if (p->fit_nbins_max > kMaxFitBins)
     return set_error(ctx, VR_ERR_INVALID_ARG, "fit_nbins_max above %d", kMaxFitBins);
-  VR_TIMED(ctx, "ell_fit", s, k_ell_fit<<<(unsigned)g.H, kFT, 0, s>>>(g.hoff, g.horder, bg.nodeoff, g.H, g.v, R, p->fit_nbins_min,
-                                          p->fit_nbins_max, p->fit_iters, halo_stats, ell));
+  if (hoff_host) {  // one launch per searched halo, in the size order
+    std::vector<uint32_t> ord(g.H);
+    VR_CUDA(ctx, cudaMemcpyAsync(ord.data(), g.horder, g.H * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    VR_CUDA(ctx, cudaStreamSynchronize(s));
+    for (int64_t i = 0; i < g.H; ++i) {
+      if (hoff_host[ord[i] + 1] - hoff_host[ord[i]] < (uint32_t)p->nsearch_min) continue;
+      k_ell_fit<<<1, kFT, 0, s>>>(g.hoff, g.horder, bg.nodeoff, i, i + 1, g.v, R, p->fit_nbins_min,
+                                  p->fit_nbins_max, p->fit_iters, halo_stats, ell);
+      VR_LAUNCHED(ctx, "k_ell_fit");
+    }
+    return VR_OK;
+  }
+  VR_TIMED(ctx, "ell_fit", s, k_ell_fit<<<(unsigned)g.H, kFT, 0, s>>>(g.hoff, g.horder, bg.nodeoff, 0, g.H, g.v, R,
+                                                                       p->fit_nbins_min, p->fit_nbins_max,
+                                                                       p->fit_iters, halo_stats, ell));
   VR_LAUNCHED(ctx, "k_ell_fit");
   return VR_OK;
 }

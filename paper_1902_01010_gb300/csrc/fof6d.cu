@@ -12,6 +12,8 @@
 // smaller than N_min get -1.
 #include <math.h>
 
+#include <vector>
+
 #include "halos.cuh"
 #include "vr_workspace.h"
 #include "unionfind.cuh"
@@ -133,8 +135,8 @@ __device__ __forceinline__ bool link6(long long dx2, float4 a, float4 b, const L
 // One warp per tile i: pairs with every later tile of the same halo (and inside tile i).
 __global__ void __launch_bounds__(128) k_link6(const uint32_t *__restrict__ toff,
                                                const uint32_t *__restrict__ coff,
-                                               const uint32_t *__restrict__ thalo, int64_t ntiles,
-                                               const int4 *__restrict__ cu,
+                                               const uint32_t *__restrict__ thalo, int64_t t0,
+                                               int64_t t1, const int4 *__restrict__ cu,
                                                const float4 *__restrict__ cv,
                                                const int4 *__restrict__ tmin,
                                                const int4 *__restrict__ tmax,
@@ -142,8 +144,8 @@ __global__ void __launch_bounds__(128) k_link6(const uint32_t *__restrict__ toff
                                                double cos2, int use_lv, int use_vt, int *parent) {
   const int lane = threadIdx.x & 31;
   const unsigned FULL = 0xffffffffu;
-  const int64_t ti = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-  if (ti >= ntiles) return;
+  const int64_t ti = t0 + (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);  // tiles [t0, t1)
+  if (ti >= t1) return;
   const uint32_t h = thalo[ti];
   const double *row = hp + (int64_t)h * VR_HALO_COLS;
   Link6 L;
@@ -156,20 +158,20 @@ __global__ void __launch_bounds__(128) k_link6(const uint32_t *__restrict__ toff
   L.cos2 = cos2;
   L.use_lv = use_lv;
   L.use_vt = use_vt;
-  const uint32_t c0h = coff[h], c1h = coff[h + 1], t0 = toff[h], t1 = toff[h + 1];
-  const uint32_t ia = c0h + 32u * ((uint32_t)ti - t0);
+  const uint32_t c0h = coff[h], c1h = coff[h + 1], th0 = toff[h], th1 = toff[h + 1];
+  const uint32_t ia = c0h + 32u * ((uint32_t)ti - th0);
   const uint32_t na = min(32u, c1h - ia);
   const bool va = (uint32_t)lane < na;
   const int4 pa = cu[va ? ia + lane : ia];
   const float4 qa = cv[va ? ia + lane : ia];
   const int4 alo = tmin[ti], ahi = tmax[ti];
   // the spatial term alone must be < 1: dx2 < lx2
-  for (uint32_t tj = (uint32_t)ti; tj < t1; ++tj) {
+  for (uint32_t tj = (uint32_t)ti; tj < th1; ++tj) {
     const int4 blo = tmin[tj], bhi = tmax[tj];
     long long gx = gap1(alo.x, ahi.x, blo.x, bhi.x), gy = gap1(alo.y, ahi.y, blo.y, bhi.y),
               gz = gap1(alo.z, ahi.z, blo.z, bhi.z);
     if ((double)(gx * gx + gy * gy + gz * gz) >= L.lx2) continue;
-    const uint32_t ib = c0h + 32u * (tj - t0);
+    const uint32_t ib = c0h + 32u * (tj - th0);
     const uint32_t nbb = min(32u, c1h - ib);
     const bool vb = (uint32_t)lane < nbb;
     const int4 pb = cu[vb ? ib + lane : ib];
@@ -257,7 +259,7 @@ vr_status fill_i32(vr_ctx *ctx, int32_t *a, int64_t n, int32_t val, cudaStream_t
 
 vr_status run_fof6d(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Arena &ar,
                     const float *ell, const double *hp, int64_t nhalo, int32_t *label6,
-                    cudaStream_t s) {
+                    cudaStream_t s, bool plain) {
   if (g.H == 0) return VR_OK;
   const int64_t H = g.H, nhp = g.NHP;
   int64_t hmax = g.n / (p->nmin > 0 ? p->nmin : 1) + 2;
@@ -303,8 +305,22 @@ vr_status run_fof6d(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Arena &ar
   const double vr2 = p->v_ratio * p->v_ratio;
   const double ct = cos(p->theta_op);
   const double cos2 = ct * ct;
-  VR_TIMED(ctx, "link6", s, k_link6<<<grid_for(ntiles, 4), 128, 0, s>>>(toff, coff, thalo, ntiles, cu, cv, tmin, tmax, hp,
-                                              vr2, cos2, p->use_lv, p->use_vr_theta, parent));
+  if (plain) {  // one launch per halo
+    std::vector<uint32_t> th(H + 1);
+    VR_CUDA(ctx, cudaMemcpyAsync(th.data(), toff, (H + 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    VR_CUDA(ctx, cudaStreamSynchronize(s));
+    for (int64_t h = 0; h < H; ++h) {
+      if (th[h + 1] == th[h]) continue;
+      k_link6<<<grid_for(th[h + 1] - th[h], 4), 128, 0, s>>>(toff, coff, thalo, th[h], th[h + 1], cu,
+                                                              cv, tmin, tmax, hp, vr2, cos2,
+                                                              p->use_lv, p->use_vr_theta, parent);
+      VR_LAUNCHED(ctx, "k_link6");
+    }
+  } else {
+    VR_TIMED(ctx, "link6", s, k_link6<<<grid_for(ntiles, 4), 128, 0, s>>>(toff, coff, thalo, 0, ntiles, cu, cv, tmin,
+                                                                       tmax, hp, vr2, cos2, p->use_lv,
+                                                                       p->use_vr_theta, parent));
+  }
   VR_LAUNCHED(ctx, "k_link6");
   k_cand_roots<<<grid_for(nc, T), T, 0, s>>>(parent, cv, nc, minidx, size);
   VR_LAUNCHED(ctx, "k_cand_roots");

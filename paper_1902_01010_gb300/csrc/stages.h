@@ -5,14 +5,16 @@
 
 namespace vr {
 size_t velden_bytes(int64_t n, int nmin);
+// hoff_host / plain: non-NULL / true selects one launch per halo (the plain form)
 vr_status run_velden(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Arena &ar, float *f_l,
-                     cudaStream_t s);
+                     cudaStream_t s, const uint32_t *hoff_host = nullptr);
 vr_status fill_f32(vr_ctx *ctx, float *a, int64_t n, float val, cudaStream_t s);
 vr_status fill_i32(vr_ctx *ctx, int32_t *a, int64_t n, int32_t val, cudaStream_t s);
 vr_status run_fit(vr_ctx *ctx, const HaloSeg &g, const Background &bg, const vr_params *p,
-                  const float *R, double *halo_stats, float *ell, cudaStream_t s);
+                  const float *R, double *halo_stats, float *ell, cudaStream_t s,
+                  const uint32_t *hoff_host = nullptr);
 size_t fof6d_bytes(int64_t n, int nmin);
 vr_status run_fof6d(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Arena &ar,
                     const float *ell, const double *hp, int64_t nhalo, int32_t *label6,
-                    cudaStream_t s);
+                    cudaStream_t s, bool plain = false);
 }  // namespace vr

@@ -3,6 +3,8 @@
 // ellfit.cu and fof6d.cu.
 #include <math.h>
 
+#include <vector>
+
 #include "stages.h"
 #include "vr_workspace.h"
 
@@ -118,7 +120,9 @@ vr_status vr_find_substructure(vr_ctx *ctx, const int32_t *pos, const float *vel
     return set_error(ctx, VR_ERR_INVALID_ARG, "NULL pointer");
   if (!(lx_sub > 0.0) || !(alpha_lv > 0.0))
     return set_error(ctx, VR_ERR_INVALID_ARG, "lx_sub and alpha_lv must be positive");
-  (void)batched;
+  if (batched != 0 && batched != 1)
+    return set_error(ctx, VR_ERR_INVALID_ARG, "batched must be 0 (one launch per halo) or 1");
+  const bool plain = batched == 0;
   cudaStream_t s = (cudaStream_t)stream;
   Arena ar(ws, ws_bytes);
   HaloSeg g;
@@ -127,18 +131,26 @@ vr_status vr_find_substructure(vr_ctx *ctx, const int32_t *pos, const float *vel
   if ((st = fill_f32(ctx, ell, n, NAN, s)) != VR_OK) return st;
   if ((st = fill_i32(ctx, label6, n, -1, s)) != VR_OK) return st;
   if ((st = build_halos(ctx, pos, vel, n, label, p->nmin, p->nse, ar, s, &g)) != VR_OK) return st;
+  std::vector<uint32_t> hoff_host;
+  if (plain && g.H > 0) {
+    hoff_host.resize(g.H + 1);
+    VR_CUDA(ctx, cudaMemcpyAsync(hoff_host.data(), g.hoff, (g.H + 1) * sizeof(uint32_t),
+                                 cudaMemcpyDeviceToHost, s));
+    VR_CUDA(ctx, cudaStreamSynchronize(s));
+  }
+  const uint32_t *hh = plain ? hoff_host.data() : nullptr;
   const size_t mark = ar.off;
-  if ((st = run_velden(ctx, g, p, ar, f_l, s)) != VR_OK) return st;
+  if ((st = run_velden(ctx, g, p, ar, f_l, s, hh)) != VR_OK) return st;
   ar.off = mark;
   Background bg;
-  if ((st = run_background(ctx, g, p, ar, f_l, R, halo_stats, &bg, s)) != VR_OK) return st;
-  if ((st = run_fit(ctx, g, bg, p, R, halo_stats, ell, s)) != VR_OK) return st;
+  if ((st = run_background(ctx, g, p, ar, f_l, R, halo_stats, &bg, s, hh)) != VR_OK) return st;
+  if ((st = run_fit(ctx, g, bg, p, R, halo_stats, ell, s, hh)) != VR_OK) return st;
   ar.off = mark;
   if (g.H > 0) {
     k_link_lengths<<<grid_for(g.H, 256), 256, 0, s>>>(halo_stats, g.H, lx_sub, alpha_lv);
     VR_LAUNCHED(ctx, "k_link_lengths");
   }
-  if ((st = run_fof6d(ctx, g, p, ar, ell, halo_stats, g.H, label6, s)) != VR_OK) return st;
+  if ((st = run_fof6d(ctx, g, p, ar, ell, halo_stats, g.H, label6, s, plain)) != VR_OK) return st;
   if (nhalo) *nhalo = g.H;
   return read_status(ctx, s, nullptr);
 }

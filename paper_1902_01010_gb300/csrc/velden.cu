@@ -23,6 +23,8 @@
 // Halos with at most N_se members use every member (one pass, no position search).
 #include <math.h>
 
+#include <vector>
+
 #include "halos.cuh"
 #include "vr_workspace.h"
 
@@ -125,12 +127,12 @@ __device__ __forceinline__ long long d2i(int4 a, int4 b) {
 // ---------------------------------------------------------------- small halos
 template <int NVM>
 __global__ void __launch_bounds__(32 * kWarps) k_velden_small(
-    const uint32_t *__restrict__ hoff, int64_t H, const float4 *__restrict__ v, int nse, int nv,
-    float *__restrict__ f_l) {
+    const uint32_t *__restrict__ hoff, int64_t h0, int64_t h1, const float4 *__restrict__ v,
+    int nse, int nv, float *__restrict__ f_l) {
   __shared__ SmallSmem<NVM> sm[kWarps];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int64_t h = (int64_t)blockIdx.x * kWarps + w;
-  if (h >= H) return;
+  int64_t h = h0 + (int64_t)blockIdx.x * kWarps + w;  // halos [h0, h1)
+  if (h >= h1) return;
   const uint32_t hs = hoff[h], he = hoff[h + 1];
   const int nh = (int)(he - hs);
   if (nh > nse) return;
@@ -233,7 +235,7 @@ __device__ __forceinline__ int bitlen64(unsigned long long x) { return x ? 64 - 
 template <int NVM>
 __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
     const uint32_t *__restrict__ hoff, const uint32_t *__restrict__ sboff,
-    const uint32_t *__restrict__ sbhalo, int64_t nbpad, const int4 *__restrict__ u,
+    const uint32_t *__restrict__ sbhalo, int64_t b0, int64_t b1, const int4 *__restrict__ u,
     const float4 *__restrict__ v, const int4 *__restrict__ bmin, const int4 *__restrict__ bmax,
     const int4 *__restrict__ smin, const int4 *__restrict__ smax, int nse, int nv,
     float *__restrict__ f_l, DevStatus *st) {
@@ -241,8 +243,8 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
   WarpSmem<NVM> &sm = reinterpret_cast<WarpSmem<NVM> *>(smem_raw)[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   const unsigned FULL = 0xffffffffu;
-  const int64_t b = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
-  if (b >= nbpad) return;
+  const int64_t b = b0 + (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);  // buckets [b0, b1)
+  if (b >= b1) return;
   const uint32_t h = sbhalo[b >> 5];
   const uint32_t hs = hoff[h], he = hoff[h + 1];
   const uint32_t nh = he - hs;
@@ -518,7 +520,7 @@ size_t velden_bytes(int64_t n, int nmin) {
 // Runs the f_l stage on an existing segmentation; f_l must already hold NaN outside
 // halos.
 vr_status run_velden(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Arena &ar, float *f_l,
-                     cudaStream_t s) {
+                     cudaStream_t s, const uint32_t *hoff_host) {
   if (g.H == 0) return VR_OK;
   const int64_t H = g.H;
   int64_t hmax = g.n / (p->nmin > 0 ? p->nmin : 1) + 2;
@@ -533,14 +535,22 @@ vr_status run_velden(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Arena &a
   if (!ar.ok()) return set_error(ctx, VR_ERR_WORKSPACE_TOO_SMALL, "workspace too small");
   const int T = 256;
   // small halos: all members are neighbours
-  if (p->nv <= 32) {
-    VR_TIMED(ctx, "velden_small", s, k_velden_small<32><<<grid_for(H, kWarps), 32 * kWarps, 0, s>>>(
-        g.hoff, H, g.v, p->nse, p->nv, f_l));
+  auto small = [&](int64_t a, int64_t z) {
+    if (p->nv <= 32)
+      k_velden_small<32><<<grid_for(z - a, kWarps), 32 * kWarps, 0, s>>>(g.hoff, a, z, g.v, p->nse, p->nv, f_l);
+    else
+      k_velden_small<kNVMax><<<grid_for(z - a, kWarps), 32 * kWarps, 0, s>>>(g.hoff, a, z, g.v, p->nse, p->nv, f_l);
+  };
+  if (hoff_host) {  // one launch per halo
+    for (int64_t h = 0; h < H; ++h) {
+      if (hoff_host[h + 1] - hoff_host[h] > (uint32_t)p->nse) continue;
+      small(h, h + 1);
+      VR_LAUNCHED(ctx, "k_velden_small");
+    }
   } else {
-    VR_TIMED(ctx, "velden_small", s, k_velden_small<kNVMax><<<grid_for(H, kWarps), 32 * kWarps, 0, s>>>(
-        g.hoff, H, g.v, p->nse, p->nv, f_l));
+    VR_TIMED(ctx, "velden_small", s, small(0, H));
+    VR_LAUNCHED(ctx, "k_velden_small");
   }
-  VR_LAUNCHED(ctx, "k_velden_small");
   k_sb_count<<<grid_for(H + 1, T), T, 0, s>>>(g.hoff, H, p->nse, sboff);
   VR_LAUNCHED(ctx, "k_sb_count");
   VR_CUDA(ctx, exclusive_scan<uint32_t>(sboff, sboff, H + 1, scr, s));
@@ -557,19 +567,33 @@ vr_status run_velden(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Arena &a
   VR_LAUNCHED(ctx, "k_bucket_boxes");
   k_superbucket_boxes<<<grid_for(nsb, T), T, 0, s>>>(nsb, bmin, bmax, smin, smax);
   VR_LAUNCHED(ctx, "k_superbucket_boxes");
-  if (p->nv <= 32) {
-    size_t shm = sizeof(WarpSmem<32>) * kWarps;
+  const size_t shm = (p->nv <= 32 ? sizeof(WarpSmem<32>) : sizeof(WarpSmem<kNVMax>)) * kWarps;
+  if (p->nv <= 32)
     VR_CUDA(ctx, cudaFuncSetAttribute(k_velden_big<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    VR_TIMED(ctx, "velden_big", s, k_velden_big<32><<<grid_for(nbpad, kWarps), 32 * kWarps, shm, s>>>(
-        g.hoff, sboff, sbhalo, nbpad, g.u, g.v, bmin, bmax, smin, smax, p->nse, p->nv, f_l,
-        ctx->d_status));
-  } else {
-    size_t shm = sizeof(WarpSmem<kNVMax>) * kWarps;
+  else
     VR_CUDA(ctx, cudaFuncSetAttribute(k_velden_big<kNVMax>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    VR_TIMED(ctx, "velden_big", s, k_velden_big<kNVMax><<<grid_for(nbpad, kWarps), 32 * kWarps, shm, s>>>(
-        g.hoff, sboff, sbhalo, nbpad, g.u, g.v, bmin, bmax, smin, smax, p->nse, p->nv, f_l,
-        ctx->d_status));
+  auto big = [&](int64_t a, int64_t z) {
+    if (p->nv <= 32)
+      k_velden_big<32><<<grid_for(z - a, kWarps), 32 * kWarps, shm, s>>>(
+          g.hoff, sboff, sbhalo, a, z, g.u, g.v, bmin, bmax, smin, smax, p->nse, p->nv, f_l,
+          ctx->d_status);
+    else
+      k_velden_big<kNVMax><<<grid_for(z - a, kWarps), 32 * kWarps, shm, s>>>(
+          g.hoff, sboff, sbhalo, a, z, g.u, g.v, bmin, bmax, smin, smax, p->nse, p->nv, f_l,
+          ctx->d_status);
+  };
+  if (hoff_host) {  // one launch per halo
+    std::vector<uint32_t> sb(H + 1);
+    VR_CUDA(ctx, cudaMemcpyAsync(sb.data(), sboff, (H + 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    VR_CUDA(ctx, cudaStreamSynchronize(s));
+    for (int64_t h = 0; h < H; ++h) {
+      if (sb[h + 1] == sb[h]) continue;
+      big(32LL * sb[h], 32LL * sb[h + 1]);
+      VR_LAUNCHED(ctx, "k_velden_big");
+    }
+    return VR_OK;
   }
+  VR_TIMED(ctx, "velden_big", s, big(0, nbpad));
   VR_LAUNCHED(ctx, "k_velden_big");
   return VR_OK;
 }

@@ -202,7 +202,7 @@ class Context:
         return label6
 
     def find_substructure(self, pos, vel, label, lx_sub: float, alpha_lv: float = 1.0,
-                          params: Params | None = None, batched: int = 0, out=None, stream=None):
+                          params: Params | None = None, batched: int = 1, out=None, stream=None):
         n = pos.shape[0]
         params = params or Params.default()
         if out is None:

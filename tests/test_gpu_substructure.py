@@ -226,3 +226,37 @@ def test_degenerate_cells_give_nan(ctx):
     assert np.isnan(R.cpu().numpy()).all()
     assert np.isnan(ell.cpu().numpy()).all()
     assert hs.shape[0] == 1 and math.isnan(hs[0, 4].item())
+
+
+@pytest.mark.parametrize("name", ["c32", "m64"])
+def test_plain_and_batched_forms_agree(ctx, name):
+    """The plain form (one launch per halo and stage) runs the same per-halo work as the
+    batched form (one launch per stage over all halos): every output is bit-identical,
+    NaN where the other is NaN."""
+    box = _box(name)
+    pos, vel = _dev(box.pos), _dev(box.vel)
+    lab = ctx.fof3d(pos, box.link_d2)
+    res = []
+    for batched in (1, 0):
+        out = ctx.find_substructure(pos, vel, lab, box.lx_sub, 1.0, batched=batched)
+        ctx.sync()
+        res.append({k: (v[: out["nhalo"]] if k == "halos" else v).cpu().numpy()
+                    for k, v in out.items() if k != "nhalo"})
+        res[-1]["nhalo"] = out["nhalo"]
+    a, b = res
+    assert a["nhalo"] == b["nhalo"] > 0
+    for k in ("f_l", "R", "ell", "halos"):
+        assert np.array_equal(a[k], b[k], equal_nan=True), k
+    assert np.array_equal(a["label6"], b["label6"])
+    assert (a["label6"] >= 0).any()
+
+
+def test_launch_form_must_be_zero_or_one(ctx):
+    from paper_1902_01010_gb300.vr import VrError
+
+    box = _box("c32")
+    pos, vel = _dev(box.pos), _dev(box.vel)
+    lab = ctx.fof3d(pos, box.link_d2)
+    with pytest.raises(VrError) as e:
+        ctx.find_substructure(pos, vel, lab, box.lx_sub, 1.0, batched=2)
+    assert e.value.code == 1
