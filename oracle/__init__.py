@@ -86,6 +86,7 @@ def _lib_():
             "or_pipeline": (i64, [vp, vp, i64, i64, dbl, dbl, ctypes.POINTER(Params), vp, vp, vp,
                                   vp, vp, vp]),
             "or_ell_bar": (dbl, [dbl]),
+            "or_field6d": (i64, [vp, vp, i64, vp, dbl, dbl, i32, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -220,6 +221,22 @@ def halo_frame(vel, members) -> np.ndarray:
     out = np.empty(4, np.float64)
     _lib_().or_halo_frame(_p(vel), _p(members), members.shape[0], _p(out))
     return out
+
+
+def field6d(pos, vel, label3, lx: float, alpha_v: float = 1.25, nmin: int = 20):
+    """Field 6DFOF of the 3DFOF groups (Sec. 2.1, Eq. fof6d). Returns (label6, rows) with
+    rows[h] = (label3, N_H, sigma_v, lx^2, lv^2) per group of >= nmin members."""
+    pos = _c(pos, np.int32)
+    vel = _c(vel, np.float32)
+    label3 = _c(label3, np.int32)
+    n = pos.shape[0]
+    lab6 = np.empty(n, np.int32)
+    rows = np.empty((n // max(nmin, 1) + 1, 5), np.float64)
+    H = _lib_().or_field6d(_p(pos), _p(vel), n, _p(label3), float(lx), float(alpha_v), nmin,
+                           _p(lab6), _p(rows))
+    if H < 0:
+        raise ValueError("bad labels")
+    return lab6, rows[:H].copy()
 
 
 def ell_bar(ell_th: float) -> float:

@@ -939,6 +939,56 @@ void or_halo_frame(const float *vel, const int32_t *members, int64_t nh, double 
   out[3] = det > 0.0 ? pow(det, 1.0 / 6.0) : 0.0;
 }
 
+/* ------------------------------------------------------- field 6DFOF (Sec. 2.1) */
+
+/* Field halos (Sec. 2.1, Eq. fof6d): every 3DFOF group of >= nmin members is split by a
+ * 6DFOF inside it. For group k, sigma_v,k = |Sigma_k|^(1/6) of its velocity dispersion
+ * tensor (Table A2, sigV; or_halo_frame) and lv = alpha_v sigma_v,k (Table 1, alpha_v);
+ * members i, j are linked iff dx^2/lx^2 + dv^2/lv^2 < 1, dx the separation of the
+ * unwrapped positions. Groups of these links with >= nmin members keep the minimum
+ * particle index as label; every other particle gets -1. A group with sigma_v,k = 0
+ * has lv = 0, so dv^2/lv^2 is +inf or NaN and no pair links (IEEE arithmetic, the
+ * paper being silent). rows (may be NULL): per 3D group, in label order,
+ * {label3, N_H, sigma_v, lx^2, lv^2}. Returns the number of 3D groups, -1 on error. */
+int64_t or_field6d(const int32_t *pos, const float *vel, int64_t n, const int32_t *label3,
+                   double lx, double alpha_v, int32_t nmin, int32_t *label6, double *rows) {
+  for (int64_t i = 0; i < n; ++i) label6[i] = -1;
+  int64_t H = or_halos(label3, n, nmin, NULL, NULL);
+  if (H < 0) return -1;
+  int64_t *off = (int64_t *)malloc((size_t)(H + 1) * sizeof(int64_t));
+  int32_t *mem = (int32_t *)malloc((size_t)(n ? n : 1) * sizeof(int32_t));
+  or_halos(label3, n, nmin, off, mem);
+  for (int64_t h = 0; h < H; ++h) {
+    const int32_t *m = mem + off[h];
+    const int64_t nh = off[h + 1] - off[h];
+    int64_t *up = (int64_t *)malloc((size_t)nh * 3 * sizeof(int64_t));
+    uint8_t *cand = (uint8_t *)malloc((size_t)nh);
+    int32_t *l6 = (int32_t *)malloc((size_t)nh * sizeof(int32_t));
+    or_unwrap(pos, m, nh, up);
+    double frame[4];
+    or_halo_frame(vel, m, nh, frame);
+    const double lv = alpha_v * frame[3];
+    double prm[5] = {lx * lx, lv * lv, frame[0], frame[1], frame[2]};
+    for (int64_t k = 0; k < nh; ++k) cand[k] = 1;
+    or_fof6d_halo(up, vel, m, nh, cand, prm, 0.0, 0.0, 1, 0, nmin, l6);
+    for (int64_t k = 0; k < nh; ++k) label6[m[k]] = l6[k];
+    if (rows) {
+      double *r = rows + 5 * h;
+      r[0] = (double)m[0];
+      r[1] = (double)nh;
+      r[2] = frame[3];
+      r[3] = prm[0];
+      r[4] = prm[1];
+    }
+    free(up);
+    free(cand);
+    free(l6);
+  }
+  free(off);
+  free(mem);
+  return H;
+}
+
 /* ------------------------------------------------------------ full pipeline */
 
 typedef struct {
