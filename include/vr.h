@@ -169,6 +169,26 @@ vr_status vr_fof6d(vr_ctx *ctx, const int32_t *pos, const float *vel, const floa
                    const vr_params *p, int32_t *label6, void *ws, size_t ws_bytes,
                    void *stream);
 
+/* Field halos (Sec. 2.1, Eq. fof6d): a 6DFOF inside every 3DFOF halo (labels of >=
+ * p->nmin members) that splits dynamically unrelated bridges. For halo k,
+ * sigma_v,k = |Sigma_k|^(1/6) of its velocity dispersion tensor (FP64, about the halo's
+ * mean velocity, divided by N_H) and lv = alpha_v sigma_v,k (Table 1: alpha_v = 1.25);
+ * members i, j are linked iff dx^2/lx^2 + dv^2/lv^2 < 1, evaluated as in vr_fof6d with
+ * every member a candidate and V_r / Theta_op off. A halo with sigma_v,k = 0 has lv = 0
+ * and links no pair (IEEE division). p->use_lv, p->use_vr_theta and p->ell_th are not
+ * used.
+ *   lx          spatial linking length in lattice units (0.2 of the mean spacing)
+ *   label6      int32 [n] out: minimum particle index of the 6D group for members of
+ *               groups of >= p->nmin, -1 otherwise (and outside halos)
+ *   halo_stats  double [n/nmin + 1][VR_HALO_COLS] out: LABEL, NH, VF*, SIGMA; LX2 = lx^2,
+ *               LV2 = (alpha_v sigma_v)^2, SEARCHED = 1; RBAR, SIGR NaN; NCELLS 0
+ *   nhalo       int64 host pointer out (may be NULL): number of 3DFOF halos
+ * Errors: VR_ERR_INVALID_ARG for lx <= 0 or alpha_v <= 0, as vr_fof6d otherwise. */
+vr_status vr_fof6d_field(vr_ctx *ctx, const int32_t *pos, const float *vel, int64_t n,
+                         const int32_t *label, double lx, double alpha_v, const vr_params *p,
+                         int32_t *label6, double *halo_stats, int64_t *nhalo, void *ws,
+                         size_t ws_bytes, void *stream);
+
 /* The substructure search of Fig. 2 (first pass) for every halo: vr_velden, then
  * vr_outlier_ratio, then the per-halo linking lengths lx2 = lx_sub^2 and
  * lv2 = (alpha_lv sigma_host)^2, then vr_fof6d on the outliers. Outputs as in those

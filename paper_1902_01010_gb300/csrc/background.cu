@@ -123,6 +123,15 @@ __global__ void __launch_bounds__(kFrameT) k_halo_frame(const uint32_t *__restri
   }
 }
 
+vr_status run_halo_frame(vr_ctx *ctx, const HaloSeg &g, int nsearch_min, double *halo_stats,
+                         cudaStream_t s) {
+  if (g.H == 0) return VR_OK;
+  VR_TIMED(ctx, "halo_frame", s, k_halo_frame<<<(unsigned)g.H, kFrameT, 0, s>>>(
+      g.hoff, g.hlabel, g.horder, 0, g.H, g.v, nsearch_min, halo_stats));
+  VR_LAUNCHED(ctx, "k_halo_frame");
+  return VR_OK;
+}
+
 // Node-capacity bound per halo (node table slots), 0 for halos not searched.
 __global__ void k_node_caps(const uint32_t *__restrict__ hoff, int64_t H, int nsearch_min,
                             double f_cell, int ncell_min, uint32_t *__restrict__ caps) {
@@ -613,9 +622,8 @@ vr_status run_background(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Aren
       VR_LAUNCHED(ctx, "k_halo_frame");
     }
   } else {
-    VR_TIMED(ctx, "halo_frame", s, k_halo_frame<<<(unsigned)H, kFrameT, 0, s>>>(
-        g.hoff, g.hlabel, g.horder, 0, H, g.v, p->nsearch_min, halo_stats));
-    VR_LAUNCHED(ctx, "k_halo_frame");
+    vr_status st = run_halo_frame(ctx, g, p->nsearch_min, halo_stats, s);
+    if (st != VR_OK) return st;
   }
   k_node_caps<<<grid_for(H + 1, 256), 256, 0, s>>>(g.hoff, H, p->nsearch_min, p->f_cell,
                                                    p->ncell_min, bg.nodeoff);

@@ -1,11 +1,14 @@
 // Phase-space linking of outliers (Sec. 2.2, Eq. linkingcriteria; with use_lv the
 // velocity term of Eq. fof6d is added).
 //
-// GB300 design: candidates (ell >= ell_th) are compacted per halo in the halo's Morton
-// order, so 32 consecutive candidates form a compact "tile" with an integer bounding box.
-// One warp owns one tile and walks the later tiles of its halo: a box gap of at least the
-// spatial linking length skips a tile pair outright; otherwise the 32 x 32 pairs are
-// tested with register shuffles. The predicate is FP64 with every operation rounded
+// The same linker serves the field 6DFOF of Sec. 2.1 (Eq. fof6d): every halo member is a
+// candidate, lx is the 3D linking length and lv = alpha_v sigma_v per halo.
+//
+// GB300 design: candidates (ell >= ell_th, or all members) are compacted per halo in the
+// halo's Morton order, so 32 consecutive candidates form a compact "tile" with an integer
+// bounding box. One warp owns one tile and walks the later tiles of its halo, 32 box
+// tests at a time across the lanes: a box gap of at least the spatial linking length
+// skips a tile pair outright; otherwise the 32 x 32 pairs are tested from shared memory. The predicate is FP64 with every operation rounded
 // explicitly (no fused multiply-add), in the fixed order stated in vr.h, so it decides
 // exactly as an FP64 reference fed the same inputs. Linked pairs are merged by the
 // lock-free union-find; labels are the minimum particle index of each group, and groups
@@ -133,6 +136,13 @@ __device__ __forceinline__ bool link6(long long dx2, float4 a, float4 b, const L
 }
 
 // One warp per tile i: pairs with every later tile of the same halo (and inside tile i).
+// The lanes test the boxes of 32 later tiles at once; each tile that comes within the
+// spatial linking length is staged in shared memory and its 32 members are read back by
+// every lane. The predicate is first evaluated in FP32 with every operand a rounded copy
+// of the FP64 one: its relative error is below 8 * 2^-24 < 5e-7, so a result outside
+// [1 - 1e-5, 1 + 1e-5] decides the FP64 comparison too; pairs inside that band, and every
+// pair when V_r / Theta_op are on, take the exact FP64 path. The FP32 route is used only
+// when lx2 and lv2 are normal FP32 numbers.
 __global__ void __launch_bounds__(128) k_link6(const uint32_t *__restrict__ toff,
                                                const uint32_t *__restrict__ coff,
                                                const uint32_t *__restrict__ thalo, int64_t t0,
@@ -142,9 +152,12 @@ __global__ void __launch_bounds__(128) k_link6(const uint32_t *__restrict__ toff
                                                const int4 *__restrict__ tmax,
                                                const double *__restrict__ hp, double vr2,
                                                double cos2, int use_lv, int use_vt, int *parent) {
-  const int lane = threadIdx.x & 31;
+  __shared__ int4 s_u[4][32];
+  __shared__ float4 s_v[4][32];
+  __shared__ int s_r[4][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const unsigned FULL = 0xffffffffu;
-  const int64_t ti = t0 + (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);  // tiles [t0, t1)
+  const int64_t ti = t0 + (int64_t)blockIdx.x * (blockDim.x / 32) + w;  // tiles [t0, t1)
   if (ti >= t1) return;
   const uint32_t h = thalo[ti];
   const double *row = hp + (int64_t)h * VR_HALO_COLS;
@@ -158,6 +171,9 @@ __global__ void __launch_bounds__(128) k_link6(const uint32_t *__restrict__ toff
   L.cos2 = cos2;
   L.use_lv = use_lv;
   L.use_vt = use_vt;
+  const bool fast = L.lx2 > 1e-30 && L.lx2 < 1e30 && (!use_lv || (L.lv2 > 1e-30 && L.lv2 < 1e30));
+  const float ilx2 = fast ? (float)(1.0 / L.lx2) : 0.0f;
+  const float ilv2 = fast && use_lv ? (float)(1.0 / L.lv2) : 0.0f;
   const uint32_t c0h = coff[h], c1h = coff[h + 1], th0 = toff[h], th1 = toff[h + 1];
   const uint32_t ia = c0h + 32u * ((uint32_t)ti - th0);
   const uint32_t na = min(32u, c1h - ia);
@@ -166,34 +182,76 @@ __global__ void __launch_bounds__(128) k_link6(const uint32_t *__restrict__ toff
   const float4 qa = cv[va ? ia + lane : ia];
   const int4 alo = tmin[ti], ahi = tmax[ti];
   // the spatial term alone must be < 1: dx2 < lx2
-  for (uint32_t tj = (uint32_t)ti; tj < th1; ++tj) {
-    const int4 blo = tmin[tj], bhi = tmax[tj];
-    long long gx = gap1(alo.x, ahi.x, blo.x, bhi.x), gy = gap1(alo.y, ahi.y, blo.y, bhi.y),
-              gz = gap1(alo.z, ahi.z, blo.z, bhi.z);
-    if ((double)(gx * gx + gy * gy + gz * gz) >= L.lx2) continue;
-    const uint32_t ib = c0h + 32u * (tj - th0);
-    const uint32_t nbb = min(32u, c1h - ib);
-    const bool vb = (uint32_t)lane < nbb;
-    const int4 pb = cu[vb ? ib + lane : ib];
-    const float4 qb = cv[vb ? ib + lane : ib];
-    for (uint32_t k = 0; k < nbb; ++k) {
-      int4 p;
-      float4 q;
-      p.x = __shfl_sync(FULL, pb.x, k);
-      p.y = __shfl_sync(FULL, pb.y, k);
-      p.z = __shfl_sync(FULL, pb.z, k);
-      q.x = __shfl_sync(FULL, qb.x, k);
-      q.y = __shfl_sync(FULL, qb.y, k);
-      q.z = __shfl_sync(FULL, qb.z, k);
+  for (uint32_t base = (uint32_t)ti; base < th1; base += 32) {
+    const uint32_t tj = base + lane;
+    bool hit = false;
+    if (tj < th1) {
+      const int4 blo = tmin[tj], bhi = tmax[tj];
+      const long long gx = gap1(alo.x, ahi.x, blo.x, bhi.x), gy = gap1(alo.y, ahi.y, blo.y, bhi.y),
+                      gz = gap1(alo.z, ahi.z, blo.z, bhi.z);
+      hit = (double)(gx * gx + gy * gy + gz * gz) < L.lx2;
+    }
+    unsigned hm = __ballot_sync(FULL, hit);
+    while (hm) {
+      const uint32_t tb = base + (uint32_t)(__ffs(hm) - 1);
+      hm &= hm - 1;
+      const uint32_t ib = c0h + 32u * (tb - th0);
+      const uint32_t nbb = min(32u, c1h - ib);
+      __syncwarp();
+      // current roots of both tiles' members: a tile pair whose members all share one set
+      // has nothing left to link (sets only ever merge, so an equal pair of roots, even
+      // stale ones, proves the two members connected)
+      const int ra = va ? uf_find(parent, (int)(ia + lane)) : -1;
+      const int rb = (uint32_t)lane < nbb ? uf_find(parent, (int)(ib + lane)) : -1;
+      if ((uint32_t)lane < nbb) {
+        s_u[w][lane] = cu[ib + lane];
+        s_v[w][lane] = cv[ib + lane];
+        s_r[w][lane] = rb;
+      }
+      const int r0 = __shfl_sync(FULL, ra, 0);
+      if (__all_sync(FULL, (!va || ra == r0) && ((uint32_t)lane >= nbb || rb == r0))) continue;
+      __syncwarp();
       if (!va) continue;
-      if (tj == (uint32_t)ti && k <= (uint32_t)lane) continue;  // each pair once
-      long long dx = (long long)pa.x - p.x, dy = (long long)pa.y - p.y, dz = (long long)pa.z - p.z;
-      long long dx2 = dx * dx + dy * dy + dz * dz;
-      // exact pre-test: dx2 >= lx2 gives dx2 / lx2 >= 1 after rounding, so q >= 1
-      if ((double)dx2 >= L.lx2) continue;
-      if (link6(dx2, qa, q, L)) uf_unite(parent, (int)(ia + lane), (int)(ib + k));
+      int rk = ra;  // a member of this lane's set, for the connected-pair skip below
+      for (uint32_t k = tb == (uint32_t)ti ? (uint32_t)lane + 1 : 0; k < nbb; ++k) {
+        const int4 p = s_u[w][k];
+        const float4 q = s_v[w][k];
+        const long long dx = (long long)pa.x - p.x, dy = (long long)pa.y - p.y,
+                        dz = (long long)pa.z - p.z;
+        const long long dx2 = dx * dx + dy * dy + dz * dz;
+        // exact pre-test: dx2 >= lx2 gives dx2 / lx2 >= 1 after rounding, so q >= 1
+        if ((double)dx2 >= L.lx2) continue;
+        bool link;
+        if (fast) {
+          float qf = (float)dx2 * ilx2;
+          if (use_lv) {
+            const float d0 = qa.x - q.x, d1 = qa.y - q.y, d2 = qa.z - q.z;
+            qf += ((d0 * d0 + d1 * d1) + d2 * d2) * ilv2;
+          }
+          if (qf >= 1.0f + 1e-5f) continue;  // also +inf; NaN falls through to FP64
+          link = (qf <= 1.0f - 1e-5f && !use_vt) ? true : link6(dx2, qa, q, L);
+        } else {
+          link = link6(dx2, qa, q, L);
+        }
+        if (link && s_r[w][k] != rk) {
+          uf_unite(parent, (int)(ia + lane), (int)(ib + k));
+          rk = min(rk, s_r[w][k]);  // now in this lane's set
+        }
+      }
     }
   }
+}
+
+// Field halos (Eq. fof6d): lx2 and lv2 = (alpha_v sigma_v)^2 for every halo, and every
+// halo marked for linking.
+__global__ void k_field_lengths(int64_t H, double lx2, double alpha_v, double *__restrict__ hs) {
+  const int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= H) return;
+  double *row = hs + h * VR_HALO_COLS;
+  const double lv = alpha_v * row[VR_H_SIGMA];
+  row[VR_H_LX2] = lx2;
+  row[VR_H_LV2] = lv * lv;
+  row[VR_H_SEARCHED] = 1.0;
 }
 
 __global__ void k_cand_init(int64_t nc, int *__restrict__ parent, int *__restrict__ minidx,
@@ -249,6 +307,14 @@ size_t fof6d_bytes(int64_t n, int nmin) {
   size_t a = scan_scratch_bytes<uint32_t>(n + 1);
   ar.take<char>(a);
   return ar.off;
+}
+
+vr_status field_lengths(vr_ctx *ctx, int64_t H, double lx2, double alpha_v, double *hs,
+                        cudaStream_t s) {
+  if (H == 0) return VR_OK;
+  k_field_lengths<<<grid_for(H, 256), 256, 0, s>>>(H, lx2, alpha_v, hs);
+  VR_LAUNCHED(ctx, "k_field_lengths");
+  return VR_OK;
 }
 
 vr_status fill_i32(vr_ctx *ctx, int32_t *a, int64_t n, int32_t val, cudaStream_t s) {
@@ -320,8 +386,8 @@ vr_status run_fof6d(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Arena &ar
     VR_TIMED(ctx, "link6", s, k_link6<<<grid_for(ntiles, 4), 128, 0, s>>>(toff, coff, thalo, 0, ntiles, cu, cv, tmin,
                                                                        tmax, hp, vr2, cos2, p->use_lv,
                                                                        p->use_vr_theta, parent));
+    VR_LAUNCHED(ctx, "k_link6");
   }
-  VR_LAUNCHED(ctx, "k_link6");
   k_cand_roots<<<grid_for(nc, T), T, 0, s>>>(parent, cv, nc, minidx, size);
   VR_LAUNCHED(ctx, "k_cand_roots");
   k_cand_label<<<grid_for(nc, T), T, 0, s>>>(parent, cv, nc, minidx, size, p->nmin, label6);

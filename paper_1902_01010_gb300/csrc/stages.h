@@ -14,6 +14,12 @@ vr_status run_fit(vr_ctx *ctx, const HaloSeg &g, const Background &bg, const vr_
                   const float *R, double *halo_stats, float *ell, cudaStream_t s,
                   const uint32_t *hoff_host = nullptr);
 size_t fof6d_bytes(int64_t n, int nmin);
+// Halo table rows (label, N_H, frame, sigma_v) for every halo, one CTA per halo.
+vr_status run_halo_frame(vr_ctx *ctx, const HaloSeg &g, int nsearch_min, double *halo_stats,
+                         cudaStream_t s);
+// Field 6DFOF lengths: LX2 = lx2, LV2 = (alpha_v sigma_v)^2, SEARCHED = 1 for every halo.
+vr_status field_lengths(vr_ctx *ctx, int64_t H, double lx2, double alpha_v, double *hs,
+                        cudaStream_t s);
 vr_status run_fof6d(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Arena &ar,
                     const float *ell, const double *hp, int64_t nhalo, int32_t *label6,
                     cudaStream_t s, bool plain = false);

@@ -106,6 +106,34 @@ vr_status vr_fof6d(vr_ctx *ctx, const int32_t *pos, const float *vel, const floa
   return run_fof6d(ctx, g, p, ar, ell, halo_params, nhalo, label6, s);
 }
 
+vr_status vr_fof6d_field(vr_ctx *ctx, const int32_t *pos, const float *vel, int64_t n,
+                         const int32_t *label, double lx, double alpha_v, const vr_params *p,
+                         int32_t *label6, double *halo_stats, int64_t *nhalo, void *ws,
+                         size_t ws_bytes, void *stream) {
+  if (!ctx) return VR_ERR_INVALID_ARG;
+  vr_status st = common_checks(ctx, n, p);
+  if (st != VR_OK) return st;
+  if (nhalo) *nhalo = 0;
+  if (n == 0) return VR_OK;
+  if (!pos || !vel || !label || !label6 || !halo_stats || !ws)
+    return set_error(ctx, VR_ERR_INVALID_ARG, "NULL pointer");
+  if (!(lx > 0.0) || !(alpha_v > 0.0))
+    return set_error(ctx, VR_ERR_INVALID_ARG, "lx and alpha_v must be positive");
+  cudaStream_t s = (cudaStream_t)stream;
+  Arena ar(ws, ws_bytes);
+  HaloSeg g;
+  if ((st = fill_i32(ctx, label6, n, -1, s)) != VR_OK) return st;
+  if ((st = build_halos(ctx, pos, vel, n, label, p->nmin, p->nse, ar, s, &g)) != VR_OK) return st;
+  if ((st = run_halo_frame(ctx, g, p->nsearch_min, halo_stats, s)) != VR_OK) return st;
+  if ((st = field_lengths(ctx, g.H, lx * lx, alpha_v, halo_stats, s)) != VR_OK) return st;
+  vr_params q = *p;
+  q.use_lv = 1;
+  q.use_vr_theta = 0;
+  if ((st = run_fof6d(ctx, g, &q, ar, nullptr, halo_stats, g.H, label6, s)) != VR_OK) return st;
+  if (nhalo) *nhalo = g.H;
+  return read_status(ctx, s, nullptr);
+}
+
 vr_status vr_find_substructure(vr_ctx *ctx, const int32_t *pos, const float *vel, int64_t n,
                                const int32_t *label, double lx_sub, double alpha_lv,
                                const vr_params *p, int batched, float *f_l, float *R,

@@ -25,7 +25,7 @@ H_LABEL, H_NH, H_SEARCHED, H_RBAR, H_SIGR, H_VFX, H_VFY, H_VFZ, H_SIGMA, H_LX2, 
 # every symbol include/vr.h declares
 EXPORTS = ("vr_params_default", "vr_create", "vr_destroy", "vr_last_error", "vr_workspace_size",
            "vr_sync", "vr_fof3d", "vr_velden", "vr_outlier_ratio", "vr_fof6d",
-           "vr_find_substructure")
+           "vr_fof6d_field", "vr_find_substructure")
 
 
 class VrError(RuntimeError):
@@ -88,6 +88,8 @@ def lib(build_if_missing: bool = True):
                 "vr_outlier_ratio": (ctypes.c_int, [vp, vp, vp, vp, i64, vp, P, vp, vp, vp,
                                                     ctypes.POINTER(i64), vp, sz, vp]),
                 "vr_fof6d": (ctypes.c_int, [vp, vp, vp, vp, i64, vp, vp, i64, P, vp, vp, sz, vp]),
+                "vr_fof6d_field": (ctypes.c_int, [vp, vp, vp, i64, vp, dbl, dbl, P, vp, vp,
+                                                  ctypes.POINTER(i64), vp, sz, vp]),
                 "vr_find_substructure": (ctypes.c_int, [vp, vp, vp, i64, vp, dbl, dbl, P,
                                                         ctypes.c_int, vp, vp, vp, vp, vp,
                                                         ctypes.POINTER(i64), vp, sz, vp]),
@@ -200,6 +202,25 @@ class Context:
                                   _ptr(halo_params), halo_params.shape[0], ctypes.byref(params),
                                   _ptr(label6), _ptr(ws), ws.numel(), _stream(stream)))
         return label6
+
+    def fof6d_field(self, pos, vel, label, lx: float, alpha_v: float = 1.25,
+                    params: Params | None = None, label6=None, halos=None, stream=None):
+        """Field 6DFOF inside every 3DFOF halo (vr_fof6d_field). Returns (label6, halo
+        table rows [nhalo, HALO_COLS])."""
+        n = pos.shape[0]
+        params = params or Params.default()
+        if label6 is None:
+            label6 = torch.empty(n, dtype=torch.int32, device=pos.device)
+        if halos is None:
+            halos = torch.empty((n // max(params.nmin, 1) + 1, HALO_COLS), dtype=torch.float64,
+                                device=pos.device)
+        nh = ctypes.c_int64()
+        ws = self.workspace(n, params)
+        self.check(lib().vr_fof6d_field(self.h, _ptr(pos), _ptr(vel), n, _ptr(label), float(lx),
+                                        float(alpha_v), ctypes.byref(params), _ptr(label6),
+                                        _ptr(halos), ctypes.byref(nh), _ptr(ws), ws.numel(),
+                                        _stream(stream)))
+        return label6, halos[: nh.value]
 
     def find_substructure(self, pos, vel, label, lx_sub: float, alpha_lv: float = 1.0,
                           params: Params | None = None, batched: int = 1, out=None, stream=None):
