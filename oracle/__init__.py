@@ -87,6 +87,7 @@ def _lib_():
                                   vp, vp, vp]),
             "or_ell_bar": (dbl, [dbl]),
             "or_field6d": (i64, [vp, vp, i64, vp, dbl, dbl, i32, vp, vp]),
+            "or_clean_groups": (i64, [vp, vp, i64, dbl, dbl, i32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -237,6 +238,15 @@ def field6d(pos, vel, label3, lx: float, alpha_v: float = 1.25, nmin: int = 20):
     if H < 0:
         raise ValueError("bad labels")
     return lab6, rows[:H].copy()
+
+
+def clean_groups(ell, label6, ell_th: float = 2.5, beta: float = 1.0, nmin: int = 20):
+    """Significance cleaning of groups (Sec. 2.2, Eq. ellsig). Returns (label6, kept)."""
+    ell = _c(ell, np.float64)
+    lab = _c(label6, np.int32).copy()
+    kept = _lib_().or_clean_groups(_p(ell), _p(lab), lab.shape[0], float(ell_th), float(beta),
+                                   nmin)
+    return lab, int(kept)
 
 
 def ell_bar(ell_th: float) -> float:

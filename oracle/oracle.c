@@ -939,6 +939,76 @@ void or_halo_frame(const float *vel, const int32_t *members, int64_t nh, double 
   out[3] = det > 0.0 ? pow(det, 1.0 / 6.0) : 0.0;
 }
 
+/* ------------------------------------------- significance cleaning (Sec. 2.2) */
+
+double or_ell_bar(double ell_th);
+
+typedef struct {
+  double ell;
+  int64_t idx;
+} or_ev;
+
+static int or_cmp_ev(const void *pa, const void *pb) {
+  const or_ev *a = (const or_ev *)pa, *b = (const or_ev *)pb;
+  if (a->ell != b->ell) return a->ell < b->ell ? -1 : 1;
+  return a->idx < b->idx ? -1 : (a->idx > b->idx);
+}
+
+/* Cleaning the catalogue (Sec. 2.2, Eq. ellsig). A group of N particles is significant
+ * when its mean ell satisfies <ell> >= ell_bar(ell_th) (1 + beta/sqrt(N)), ell_bar the
+ * tail mean of Eq. ellsig (or_ell_bar). A group that is not loses its particles in order
+ * of smallest ell (ties: smaller particle index first) until it is; a group left with
+ * fewer than nmin particles is removed. Removed particles get -1; the particles kept get
+ * the minimum particle index among them. The mean is (sum of the kept ell) / N in FP64,
+ * the threshold ell_bar * (1 + beta / sqrt(N)).
+ * label6 [n] in/out (groups: equal labels >= 0), ell [n]. Returns the groups kept. */
+int64_t or_clean_groups(const double *ell, int32_t *label6, int64_t n, double ell_th,
+                        double beta, int32_t nmin) {
+  const double lbar = or_ell_bar(ell_th);
+  /* group the particles by label (counting sort on the label value) */
+  int64_t *count = (int64_t *)calloc((size_t)(n + 1), sizeof(int64_t));
+  for (int64_t i = 0; i < n; ++i)
+    if (label6[i] >= 0) count[label6[i] + 1]++;
+  for (int64_t l = 0; l < n; ++l) count[l + 1] += count[l];
+  or_ev *ev = (or_ev *)malloc((size_t)(count[n] ? count[n] : 1) * sizeof(or_ev));
+  int64_t *fill = (int64_t *)calloc((size_t)(n ? n : 1), sizeof(int64_t));
+  for (int64_t i = 0; i < n; ++i) {
+    if (label6[i] < 0) continue;
+    int64_t l = label6[i];
+    ev[count[l] + fill[l]].ell = ell[i];
+    ev[count[l] + fill[l]].idx = i;
+    fill[l]++;
+  }
+  int64_t kept = 0;
+  for (int64_t l = 0; l < n; ++l) {
+    const int64_t b = count[l], N = count[l + 1] - count[l];
+    if (N == 0) continue;
+    or_ev *g = ev + b;
+    qsort(g, (size_t)N, sizeof(or_ev), or_cmp_ev);
+    double sum = 0.0;
+    for (int64_t k = 0; k < N; ++k) sum += g[k].ell;
+    int64_t cut = -1; /* particles removed */
+    for (int64_t k = 0; k < N; ++k) {
+      const int64_t m = N - k;
+      const double mean = sum / (double)m;
+      const double thr = lbar * (1.0 + beta / sqrt((double)m));
+      if (mean >= thr) { cut = k; break; }
+      sum -= g[k].ell;
+    }
+    const int keep = cut >= 0 && N - cut >= nmin;
+    int64_t newlab = n;
+    if (keep)
+      for (int64_t k = cut; k < N; ++k) newlab = g[k].idx < newlab ? g[k].idx : newlab;
+    for (int64_t k = 0; k < N; ++k)
+      label6[g[k].idx] = (keep && k >= cut) ? (int32_t)newlab : -1;
+    kept += keep;
+  }
+  free(fill);
+  free(ev);
+  free(count);
+  return kept;
+}
+
 /* ------------------------------------------------------- field 6DFOF (Sec. 2.1) */
 
 /* Field halos (Sec. 2.1, Eq. fof6d): every 3DFOF group of >= nmin members is split by a
