@@ -202,6 +202,28 @@ vr_status vr_find_substructure(vr_ctx *ctx, const int32_t *pos, const float *vel
                                float *ell, int32_t *label6, double *halo_stats, int64_t *nhalo,
                                void *ws, size_t ws_bytes, void *stream);
 
+/* Cleaning of outlier groups (Sec. 2.2, "Cleaning the catalogue", Eq. ellsig). A group
+ * of N particles (equal labels >= 0 in label6) is significant iff
+ *   <ell> >= ell_bar(p->ell_th) (1 + beta/sqrt(N)),
+ * ell_bar(t) = sqrt(2/pi) exp(-t^2/2) / erfc(t/sqrt 2), the mean of a unit Gaussian
+ * above t (2.822744797663897 at t = 2.5). A group that is not significant loses its
+ * particles in order of smallest ell (ties: smaller particle index first) until it is;
+ * a group left with fewer than p->nmin particles is removed. Removed particles get -1;
+ * the particles kept get the minimum particle index among them. <ell> is the FP64 sum
+ * of the FP32 ell values (exact, hence independent of the order of additions, while a
+ * group's sum stays below 2^53 times the FP32 spacing of its smallest ell: 2^31 for
+ * ell >= 2) divided by N; the threshold is ell_bar * (1 + beta / sqrt(N)), each
+ * operation rounded once.
+ *   ell      float32 [n]; must not be NaN for grouped particles (outlier groups hold
+ *            ell >= ell_th by construction)
+ *   beta     beta_ell >= 0 (Table 1: 1)
+ *   label6   int32 [n] in/out
+ *   ngroups  int64 host pointer out (may be NULL): groups kept
+ * This call synchronises `stream`. Errors: VR_ERR_INVALID_ARG for beta < 0. */
+vr_status vr_clean_groups(vr_ctx *ctx, const float *ell, int64_t n, const vr_params *p,
+                          double beta, int32_t *label6, int64_t *ngroups, void *ws,
+                          size_t ws_bytes, void *stream);
+
 /* ----------------------------------------------------- allocation-free 3D FOF
  * No counterpart in the paper. For callers that cannot allocate device memory at all
  * (for example code running where cudaMalloc is forbidden or unavailable, such as inside
@@ -228,7 +250,7 @@ vr_status vr_fof3d_noalloc(const int32_t *pos, int64_t n, int64_t link_d2, int32
  * (no counterpart in the paper: instrumentation of this library)
  * Per-kernel device timing with CUDA events recorded on the launching stream; off by
  * default. Kernel names: "fof_link", "velden_big", "velden_small", "halo_frame",
- * "cells_build", "cells_build_big", "ratio", "ell_fit", "link6". */
+ * "cells_build", "cells_build_big", "ratio", "ell_fit", "link6", "clean". */
 
 /* Enables (1) or disables (0) event timing of the named kernels for this context. */
 vr_status vr_timing_enable(vr_ctx *ctx, int enable);

@@ -14,6 +14,8 @@ size_t ws_substructure(int64_t n, const vr_params *p) {
   size_t a = velden_bytes(n, p->nmin), b = background_bytes(n, p), c = fof6d_bytes(n, p->nmin);
   size_t m = a > b ? a : b;
   m = m > c ? m : c;
+  const size_t cl = clean_bytes(n);
+  m = m > cl ? m : cl;
   return halo_seg_bytes(n, p->nmin) + m + 4096;
 }
 
@@ -132,6 +134,20 @@ vr_status vr_fof6d_field(vr_ctx *ctx, const int32_t *pos, const float *vel, int6
   if ((st = run_fof6d(ctx, g, &q, ar, nullptr, halo_stats, g.H, label6, s)) != VR_OK) return st;
   if (nhalo) *nhalo = g.H;
   return read_status(ctx, s, nullptr);
+}
+
+vr_status vr_clean_groups(vr_ctx *ctx, const float *ell, int64_t n, const vr_params *p,
+                          double beta, int32_t *label6, int64_t *ngroups, void *ws,
+                          size_t ws_bytes, void *stream) {
+  if (!ctx) return VR_ERR_INVALID_ARG;
+  vr_status st = common_checks(ctx, n, p);
+  if (st != VR_OK) return st;
+  if (ngroups) *ngroups = 0;
+  if (n == 0) return VR_OK;
+  if (!ell || !label6 || !ws) return set_error(ctx, VR_ERR_INVALID_ARG, "NULL pointer");
+  if (!(beta >= 0.0)) return set_error(ctx, VR_ERR_INVALID_ARG, "beta must be >= 0");
+  Arena ar(ws, ws_bytes);
+  return run_clean(ctx, ell, n, p, beta, label6, ngroups, ar, (cudaStream_t)stream);
 }
 
 vr_status vr_find_substructure(vr_ctx *ctx, const int32_t *pos, const float *vel, int64_t n,

@@ -25,7 +25,7 @@ H_LABEL, H_NH, H_SEARCHED, H_RBAR, H_SIGR, H_VFX, H_VFY, H_VFZ, H_SIGMA, H_LX2, 
 # every symbol include/vr.h declares
 EXPORTS = ("vr_params_default", "vr_create", "vr_destroy", "vr_last_error", "vr_workspace_size",
            "vr_sync", "vr_fof3d", "vr_velden", "vr_outlier_ratio", "vr_fof6d",
-           "vr_fof6d_field", "vr_find_substructure")
+           "vr_fof6d_field", "vr_clean_groups", "vr_find_substructure")
 
 
 class VrError(RuntimeError):
@@ -90,6 +90,8 @@ def lib(build_if_missing: bool = True):
                 "vr_fof6d": (ctypes.c_int, [vp, vp, vp, vp, i64, vp, vp, i64, P, vp, vp, sz, vp]),
                 "vr_fof6d_field": (ctypes.c_int, [vp, vp, vp, i64, vp, dbl, dbl, P, vp, vp,
                                                   ctypes.POINTER(i64), vp, sz, vp]),
+                "vr_clean_groups": (ctypes.c_int, [vp, vp, i64, P, dbl, vp, ctypes.POINTER(i64),
+                                                   vp, sz, vp]),
                 "vr_find_substructure": (ctypes.c_int, [vp, vp, vp, i64, vp, dbl, dbl, P,
                                                         ctypes.c_int, vp, vp, vp, vp, vp,
                                                         ctypes.POINTER(i64), vp, sz, vp]),
@@ -221,6 +223,19 @@ class Context:
                                         _ptr(halos), ctypes.byref(nh), _ptr(ws), ws.numel(),
                                         _stream(stream)))
         return label6, halos[: nh.value]
+
+    def clean_groups(self, ell, label6, params: Params | None = None, beta: float = 1.0,
+                     stream=None):
+        """Significance cleaning of the groups in label6, in place (vr_clean_groups).
+        Returns the number of groups kept."""
+        n = label6.shape[0]
+        params = params or Params.default()
+        ng = ctypes.c_int64()
+        ws = self.workspace(n, params)
+        self.check(lib().vr_clean_groups(self.h, _ptr(ell), n, ctypes.byref(params), float(beta),
+                                         _ptr(label6), ctypes.byref(ng), _ptr(ws), ws.numel(),
+                                         _stream(stream)))
+        return ng.value
 
     def find_substructure(self, pos, vel, label, lx_sub: float, alpha_lv: float = 1.0,
                           params: Params | None = None, batched: int = 1, out=None, stream=None):
