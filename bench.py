@@ -4,7 +4,7 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload c512] [--form batched|plain] [--plain-steps P]
-                    [--no-cpu-baseline]
+                    [--no-next-rows] [--no-cpu-baseline]
 
 One step = vr_fof3d + vr_find_substructure over the whole box, inputs resident in HBM
 (3.2 GB of positions and velocities, far above the 129 MB L2, so no flush is needed
@@ -14,7 +14,9 @@ the slowest rank's time. Rank 0 prints one JSON line.
 
 The headline runs the batched form (each stage one launch over all halos); the same
 inputs are then timed in the plain form (each stage launched once per halo) and reported
-under "plain_form".
+under "plain_form". Field 6DFOF of the 3DFOF halos and the significance cleaning of the
+step's outlier groups are timed afterwards on the same box and reported under
+"next_rows" (outside the headline).
 
 --impl reference times the FP64 C oracle (the path's reference implementation) on the
 host cores, one step = the oracle pipeline over a bounded sample of the workload (a 64^3
@@ -269,6 +271,48 @@ def run_ours(args):
                "h2d_bytes_per_step": int(hpos.numel() * 4 + hvel.numel() * 4),
                "d2h_bytes_per_step": int(hl3.numel() * 4 + hl6.numel() * 4)}
 
+    # ---- rows beyond the headline step, on the same box (timed separately, 3 calls each):
+    #      field 6DFOF of the 3DFOF halos (Sec. 2.1) and significance cleaning of the
+    #      outlier groups the step produced (Sec. 2.2, Eq. ellsig)
+    next_rows = None
+    if args.next_rows:
+        lx = 0.2 * synth.mean_spacing(box.n)
+        l6f = torch.empty(box.n, dtype=torch.int32, device=dev)
+        halos_f = torch.empty((box.n // P.nmin + 1, 12), dtype=torch.float64, device=dev)
+        l6c = out["label6"].clone()
+
+        def field():
+            ctx.fof6d_field(pos, vel, lab, lx, 1.25, P, label6=l6f, halos=halos_f)
+
+        def clean():
+            l6c.copy_(out["label6"])
+            return ctx.clean_groups(out["ell"], l6c, P, 1.0)
+
+        field()
+        clean()
+        ctx.sync()
+        res = {}
+        for name, f in (("field_6dfof", field), ("clean_groups", clean)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            for _ in range(3):
+                f()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            res[name] = {"ms": e0.elapsed_time(e1) / 3}
+        ng = clean()
+        a = l6f.cpu().numpy()
+        res["field_6dfof"].update({"particles_per_s": box.n / (res["field_6dfof"]["ms"] / 1e3),
+                                   "particles_in_6d_groups": int((a >= 0).sum()),
+                                   "groups": int(len(np.unique(a[a >= 0]))),
+                                   "alpha_v": 1.25, "l_x": "0.2 mean spacing"})
+        res["clean_groups"].update({"groups_kept": int(ng),
+                                    "groups_in": int(len(np.unique(
+                                        out["label6"].cpu().numpy()[out["label6"].cpu().numpy() >= 0]))),
+                                    "beta": 1.0})
+        next_rows = res
+
     # ---- the other launch form on the same inputs: one launch per halo and stage
     plain = None
     if batched and args.plain_steps > 0:
@@ -347,6 +391,7 @@ def run_ours(args):
         "clocks": clk,
         "kernel_share_of_step": shares,
         "plain_form": plain,
+        "next_rows": next_rows,
     }
     print(json.dumps(line), flush=True)
 
@@ -407,6 +452,8 @@ def main():
                     help="timed steps of the plain form (one launch per halo and stage) "
                          "reported beside a batched headline; 0 skips it")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-next-rows", dest="next_rows", action="store_false",
+                    help="skip timing field 6DFOF and group cleaning after the headline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
