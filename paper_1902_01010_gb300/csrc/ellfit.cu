@@ -24,6 +24,9 @@ namespace vr {
 namespace {
 
 constexpr int kFT = 256;
+#ifndef VR_FIT_MINB
+#define VR_FIT_MINB 4  // resident CTAs per SM the register budget is set for
+#endif
 constexpr int kMaxFitBins = 1024;
 
 __device__ __forceinline__ uint32_t fkey(float x) {
@@ -141,14 +144,49 @@ __device__ bool solve4(double M[4][4], const double *b, double *x) {
   return true;
 }
 
+// R of every halo slot, in slot order (the selections below read it many times).
+__global__ void k_gather_r(const float4 *__restrict__ v, const float *__restrict__ R, int64_t nhp,
+                           float *__restrict__ Rs) {
+  const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < nhp) Rs[m] = R[__float_as_int(v[m].w)];
+}
+
+// The key of rank k - 1 given the key `a` of rank k (0-based, k >= 1) among the valid
+// keys: `a` itself if fewer than k keys lie below it (a run of equal keys), else the
+// largest key below `a`. One pass instead of a second selection.
+template <class Get>
+__device__ unsigned long long block_prev_rank(int n, int k, unsigned long long a, Get get,
+                                              unsigned long long *s_max, int *s_cnt) {
+  const int t = threadIdx.x;
+  if (t == 0) {
+    *s_max = 0ULL;
+    *s_cnt = 0;
+  }
+  __syncthreads();
+  unsigned long long mx = 0ULL;
+  int c = 0;
+  for (int i = t; i < n; i += kFT) {
+    unsigned long long key;
+    if (!get(i, key) || key >= a) continue;
+    ++c;
+    mx = key > mx ? key : mx;
+  }
+  atomicAdd(s_cnt, c);
+  atomicMax(s_max, mx);
+  __syncthreads();
+  const unsigned long long r = *s_cnt < k ? a : *s_max;
+  __syncthreads();
+  return r;
+}
+
 }  // namespace
 
-__global__ void __launch_bounds__(kFT) k_ell_fit(const uint32_t *__restrict__ hoff,
+__global__ void __launch_bounds__(kFT, VR_FIT_MINB) k_ell_fit(const uint32_t *__restrict__ hoff,
                                                  const uint32_t *__restrict__ horder,
                                                  const uint32_t *__restrict__ nodeoff,
                                                  int64_t first, int64_t last,
                                                  const float4 *__restrict__ v,
-                                                 const float *__restrict__ R, int nb_min,
+                                                 const float *__restrict__ Rs, int nb_min,
                                                  int nb_max, int iters, double *__restrict__ hs,
                                                  float *__restrict__ ell) {
   __shared__ uint32_t s_dig[256];
@@ -158,13 +196,15 @@ __global__ void __launch_bounds__(kFT) k_ell_fit(const uint32_t *__restrict__ ho
   __shared__ int s_cnt[kMaxFitBins];
   __shared__ int s_n;
   __shared__ double s_par[8];
+  __shared__ unsigned long long s_max;
+  __shared__ int s_lt;
   if (first + (int64_t)blockIdx.x >= last) return;
   const int64_t h = horder[first + blockIdx.x];  // largest halos first
   if (nodeoff[h + 1] == nodeoff[h]) return;  // not searched
   const uint32_t hb = hoff[h], he = hoff[h + 1];
   const int nh = (int)(he - hb);
   const int t = threadIdx.x;
-  auto rval = [&](int i) { return R[__float_as_int(v[hb + i].w)]; };
+  auto rval = [&](int i) { return Rs[hb + i]; };
   // number of finite values
   if (t == 0) s_n = 0;
   __syncthreads();
@@ -190,11 +230,12 @@ __global__ void __launch_bounds__(kFT) k_ell_fit(const uint32_t *__restrict__ ho
   };
   double med;
   {
-    float a = fkey_inv((uint32_t)block_select(nh, n / 2, 32, getf, s_dig, s_scan, &s_pre, &s_rank));
+    const unsigned long long ka = block_select(nh, n / 2, 32, getf, s_dig, s_scan, &s_pre, &s_rank);
+    float a = fkey_inv((uint32_t)ka);
     if (n & 1) {
       med = (double)a;
     } else {
-      float b = fkey_inv((uint32_t)block_select(nh, n / 2 - 1, 32, getf, s_dig, s_scan, &s_pre, &s_rank));
+      float b = fkey_inv((uint32_t)block_prev_rank(nh, n / 2, ka, getf, &s_max, &s_lt));
       med = 0.5 * ((double)b + (double)a);
     }
   }
@@ -206,11 +247,12 @@ __global__ void __launch_bounds__(kFT) k_ell_fit(const uint32_t *__restrict__ ho
   };
   double mad;
   {
-    double a = __longlong_as_double((long long)block_select(nh, n / 2, 64, getd, s_dig, s_scan, &s_pre, &s_rank));
+    const unsigned long long ka = block_select(nh, n / 2, 64, getd, s_dig, s_scan, &s_pre, &s_rank);
+    double a = __longlong_as_double((long long)ka);
     if (n & 1) {
       mad = a;
     } else {
-      double b = __longlong_as_double((long long)block_select(nh, n / 2 - 1, 64, getd, s_dig, s_scan, &s_pre, &s_rank));
+      double b = __longlong_as_double((long long)block_prev_rank(nh, n / 2, ka, getd, &s_max, &s_lt));
       mad = 0.5 * (b + a);
     }
     mad = __dmul_rn(1.4826, mad);
@@ -307,7 +349,7 @@ __global__ void __launch_bounds__(kFT) k_ell_fit(const uint32_t *__restrict__ ho
   const double rbar = s_par[0], sigr = s_par[1];
   for (int i = t; i < nh; i += kFT) {
     const int pi = __float_as_int(v[hb + i].w);
-    ell[pi] = (float)(((double)R[pi] - rbar) / sigr);
+    ell[pi] = (float)(((double)Rs[hb + i] - rbar) / sigr);
   }
 }
 
@@ -316,19 +358,22 @@ vr_status run_fit(vr_ctx *ctx, const HaloSeg &g, const Background &bg, const vr_
   if (g.H == 0) return VR_OK;
   if (p->fit_nbins_max > kMaxFitBins)
     return set_error(ctx, VR_ERR_INVALID_ARG, "fit_nbins_max above %d", kMaxFitBins);
+  float *Rs = reinterpret_cast<float *>(g.scratch_u32_a);  // [n + 1] words, unused here
+  k_gather_r<<<grid_for(g.NHP, 256), 256, 0, s>>>(g.v, R, g.NHP, Rs);
+  VR_LAUNCHED(ctx, "k_gather_r");
   if (hoff_host) {  // one launch per searched halo, in the size order
     std::vector<uint32_t> ord(g.H);
     VR_CUDA(ctx, cudaMemcpyAsync(ord.data(), g.horder, g.H * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     VR_CUDA(ctx, cudaStreamSynchronize(s));
     for (int64_t i = 0; i < g.H; ++i) {
       if (hoff_host[ord[i] + 1] - hoff_host[ord[i]] < (uint32_t)p->nsearch_min) continue;
-      k_ell_fit<<<1, kFT, 0, s>>>(g.hoff, g.horder, bg.nodeoff, i, i + 1, g.v, R, p->fit_nbins_min,
+      k_ell_fit<<<1, kFT, 0, s>>>(g.hoff, g.horder, bg.nodeoff, i, i + 1, g.v, Rs, p->fit_nbins_min,
                                   p->fit_nbins_max, p->fit_iters, halo_stats, ell);
       VR_LAUNCHED(ctx, "k_ell_fit");
     }
     return VR_OK;
   }
-  VR_TIMED(ctx, "ell_fit", s, k_ell_fit<<<(unsigned)g.H, kFT, 0, s>>>(g.hoff, g.horder, bg.nodeoff, 0, g.H, g.v, R,
+  VR_TIMED(ctx, "ell_fit", s, k_ell_fit<<<(unsigned)g.H, kFT, 0, s>>>(g.hoff, g.horder, bg.nodeoff, 0, g.H, g.v, Rs,
                                                                        p->fit_nbins_min, p->fit_nbins_max,
                                                                        p->fit_iters, halo_stats, ell));
   VR_LAUNCHED(ctx, "k_ell_fit");
