@@ -88,6 +88,8 @@ def _lib_():
             "or_ell_bar": (dbl, [dbl]),
             "or_field6d": (i64, [vp, vp, i64, vp, dbl, dbl, i32, vp, vp]),
             "or_clean_groups": (i64, [vp, vp, i64, dbl, dbl, i32]),
+            "or_grow_halo": (ctypes.c_int, [vp, vp, vp, i64, vp, vp, vp, dbl, dbl, dbl,
+                                            ctypes.c_int, ctypes.c_int, vp, dbl, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -247,6 +249,45 @@ def clean_groups(ell, label6, ell_th: float = 2.5, beta: float = 1.0, nmin: int 
     kept = _lib_().or_clean_groups(_p(ell), _p(lab), lab.shape[0], float(ell_th), float(beta),
                                    nmin)
     return lab, int(kept)
+
+
+GROW_DEFAULTS = (1.0, 2.0, 1.0, 1.0)  # gamma_ell, gamma_x, gamma_vr, gamma_theta (Table A1)
+F_MERGE = 0.25  # f_merge,th (Sec. 2.2)
+
+
+def grow_halo(upos, vel, members, ell, lab1, prm, ell_th=2.5, v_ratio=2.0,
+              theta_op=0.1 * math.pi, use_lv=1, use_vt=1, gam=GROW_DEFAULTS,
+              f_merge=F_MERGE) -> np.ndarray:
+    """Two-stage linking inside one halo (Sec. 2.2): relaxed growth of the stage-1
+    groups lab1 and the merge threshold. ell, lab1 per member; members ascending."""
+    upos = _c(upos, np.int64)
+    vel = _c(vel, np.float32)
+    members = _c(members, np.int32)
+    ell = _c(ell, np.float64)
+    lab1 = _c(lab1, np.int32)
+    prm = _c(prm, np.float64)
+    g = _c(gam, np.float64)
+    out = np.empty(members.shape[0], np.int32)
+    _lib_().or_grow_halo(_p(upos), _p(vel), _p(members), members.shape[0], _p(ell), _p(lab1),
+                         _p(prm), ell_th, v_ratio, theta_op, use_lv, use_vt, _p(g), f_merge,
+                         _p(out))
+    return out
+
+
+def two_stage(pos, vel, label3, ell, label6, halo_rows, nmin=20, **kw) -> np.ndarray:
+    """grow_halo over every searched halo of a box (rows as the halo table: label, N_H,
+    searched, ..., vframe at 5-7, lx2 at 9, lv2 at 10). Returns the final labels."""
+    out = np.asarray(label6, np.int32).copy()
+    off, mem = halos(label3, nmin)
+    for h in range(len(off) - 1):
+        r = halo_rows[h]
+        if r[2] == 0:
+            continue
+        m = mem[off[h]:off[h + 1]]
+        prm = np.array([r[9], r[10], r[5], r[6], r[7]])
+        out[m] = grow_halo(unwrap(pos, m), vel, m, np.asarray(ell, np.float64)[m],
+                           np.asarray(label6, np.int32)[m], prm, **kw)
+    return out
 
 
 def ell_bar(ell_th: float) -> float:

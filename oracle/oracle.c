@@ -1009,6 +1009,164 @@ int64_t or_clean_groups(const double *ell, int32_t *label6, int64_t n, double el
   return kept;
 }
 
+/* ------------------------------------------------- two-stage linking (Sec. 2.2) */
+
+typedef struct {
+  int64_t a, b;
+} or_pair;
+
+/* Slot of particle index x among ascending members, -1 if absent. */
+static int64_t or_slot(const int32_t *members, int64_t nh, int64_t x) {
+  int64_t lo = 0, hi = nh;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) / 2;
+    if (members[mid] < x) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo < nh && members[lo] == x ? lo : -1;
+}
+
+static int or_cmp_pair(const void *pa, const void *pb) {
+  const or_pair *x = (const or_pair *)pa, *y = (const or_pair *)pb;
+  if (x->a != y->a) return x->a < y->a ? -1 : 1;
+  return x->b < y->b ? -1 : (x->b > y->b);
+}
+
+/* Two-stage linking inside one halo (Sec. 2.2, "Linking particles": conservative
+ * criteria find the candidate substructures, relaxed criteria then link previously
+ * untagged particles to them; substructures are joined only when the new connections
+ * exceed f_merge times the original size of either).
+ *   lab1  [nh] stage-1 labels of the members (minimum particle index of the group, -1
+ *         for untagged members); ell [nh] their ell
+ *   prm   (lx2, lv2, vframe_x, vframe_y, vframe_z) of the conservative pass
+ *   gam   (gamma_ell, gamma_x, gamma_vr, gamma_theta): the relaxed pass takes
+ *         candidates with ell >= ell_th / gamma_ell (and every tagged member), and links
+ *         with lx2 gamma_x^2, V_r gamma_vr, Theta_op gamma_theta (lv2, frame unchanged)
+ * Steps, in this order:
+ *  1. the untagged candidates form connected components under the relaxed links among
+ *     themselves;
+ *  2. a component joins the stage-1 group with the most relaxed links between its
+ *     members and the group's members (ties: the smaller label); with no such link it
+ *     stays untagged;
+ *  3. two grown groups A, B are joined iff the number of relaxed links between their
+ *     members exceeds f_merge N_o(A) or f_merge N_o(B), N_o the stage-1 size; joins are
+ *     transitive;
+ *  4. every final group is labelled with its minimum particle index; untagged members
+ *     get -1.
+ * members ascending (as or_halos gives them). out [nh]: final labels. Returns 0. */
+int or_grow_halo(const int64_t *upos, const float *vel, const int32_t *members, int64_t nh,
+                 const double *ell, const int32_t *lab1, const double *prm, double ell_th,
+                 double v_ratio, double theta_op, int use_lv, int use_vt, const double *gam,
+                 double f_merge, int32_t *out) {
+  for (int64_t i = 0; i < nh; ++i) out[i] = -1;
+  if (nh <= 0) return 0;
+  const double thr = ell_th / gam[0];
+  const double prm2[5] = {prm[0] * gam[1] * gam[1], prm[1], prm[2], prm[3], prm[4]};
+  const double vr = v_ratio * gam[2], ct = cos(theta_op * gam[3]);
+  const double vr2 = vr * vr, cos2 = ct * ct;
+  uint8_t *cand = (uint8_t *)malloc((size_t)nh);
+  for (int64_t i = 0; i < nh; ++i) cand[i] = lab1[i] >= 0 || ell[i] >= thr;
+  /* the relaxed links, once */
+  int64_t ne = 0, cap = 1024;
+  or_pair *e = (or_pair *)malloc((size_t)cap * sizeof(or_pair));
+  for (int64_t i = 0; i < nh; ++i) {
+    if (!cand[i]) continue;
+    for (int64_t j = i + 1; j < nh; ++j) {
+      if (!cand[j]) continue;
+      int64_t d2 = 0;
+      for (int c = 0; c < 3; ++c) {
+        int64_t d = upos[3 * i + c] - upos[3 * j + c];
+        d2 += d * d;
+      }
+      if (!or_link6(d2, vel + 3 * (int64_t)members[i], vel + 3 * (int64_t)members[j], prm2,
+                    vr2, cos2, use_lv, use_vt))
+        continue;
+      if (ne == cap) {
+        cap *= 2;
+        e = (or_pair *)realloc(e, (size_t)cap * sizeof(or_pair));
+      }
+      e[ne].a = i;
+      e[ne].b = j;
+      ne++;
+    }
+  }
+  /* 1. components of the untagged candidates */
+  int64_t *parent = (int64_t *)malloc((size_t)nh * sizeof(int64_t));
+  for (int64_t i = 0; i < nh; ++i) parent[i] = i;
+  for (int64_t k = 0; k < ne; ++k)
+    if (lab1[e[k].a] < 0 && lab1[e[k].b] < 0) or_union(parent, e[k].a, e[k].b);
+  /* 2. links between components and groups: (component root, group label) pairs */
+  or_pair *cg = (or_pair *)malloc((size_t)(ne ? ne : 1) * sizeof(or_pair));
+  int64_t ncg = 0;
+  for (int64_t k = 0; k < ne; ++k) {
+    int64_t a = e[k].a, b = e[k].b;
+    if ((lab1[a] < 0) == (lab1[b] < 0)) continue;
+    int64_t u = lab1[a] < 0 ? a : b, t = lab1[a] < 0 ? b : a;
+    cg[ncg].a = or_find(parent, u);
+    cg[ncg].b = lab1[t];
+    ncg++;
+  }
+  qsort(cg, (size_t)ncg, sizeof(or_pair), or_cmp_pair);
+  int64_t *best = (int64_t *)malloc((size_t)nh * sizeof(int64_t));
+  int64_t *bestn = (int64_t *)calloc((size_t)nh, sizeof(int64_t));
+  for (int64_t i = 0; i < nh; ++i) best[i] = -1;
+  for (int64_t k = 0; k < ncg;) {
+    int64_t k2 = k;
+    while (k2 < ncg && cg[k2].a == cg[k].a && cg[k2].b == cg[k].b) k2++;
+    int64_t c = cg[k].a, cnt = k2 - k;
+    if (cnt > bestn[c]) { /* groups ascend within a component: ties keep the smaller */
+      bestn[c] = cnt;
+      best[c] = cg[k].b;
+    }
+    k = k2;
+  }
+  int64_t *grown = (int64_t *)malloc((size_t)nh * sizeof(int64_t));
+  for (int64_t i = 0; i < nh; ++i) {
+    if (lab1[i] >= 0) grown[i] = lab1[i];
+    else if (cand[i]) grown[i] = best[or_find(parent, i)];
+    else grown[i] = -1;
+  }
+  /* 3. joins between grown groups; group labels are particle indices of members, mapped
+   *    to the member slot of that particle for a union-find over slots */
+  int64_t *n0 = (int64_t *)calloc((size_t)nh, sizeof(int64_t));
+  for (int64_t i = 0; i < nh; ++i)
+    if (lab1[i] >= 0) n0[or_slot(members, nh, lab1[i])]++;
+  or_pair *ab = (or_pair *)malloc((size_t)(ne ? ne : 1) * sizeof(or_pair));
+  int64_t nab = 0;
+  for (int64_t k = 0; k < ne; ++k) {
+    int64_t ga = grown[e[k].a], gb = grown[e[k].b];
+    if (ga < 0 || gb < 0 || ga == gb) continue;
+    ab[nab].a = ga < gb ? ga : gb;
+    ab[nab].b = ga < gb ? gb : ga;
+    nab++;
+  }
+  qsort(ab, (size_t)nab, sizeof(or_pair), or_cmp_pair);
+  int64_t *gpar = (int64_t *)malloc((size_t)nh * sizeof(int64_t));
+  for (int64_t i = 0; i < nh; ++i) gpar[i] = i;
+  for (int64_t k = 0; k < nab;) {
+    int64_t k2 = k;
+    while (k2 < nab && ab[k2].a == ab[k].a && ab[k2].b == ab[k].b) k2++;
+    const int64_t sa = or_slot(members, nh, ab[k].a), sb = or_slot(members, nh, ab[k].b);
+    double cnt = (double)(k2 - k);
+    if (cnt > f_merge * (double)n0[sa] || cnt > f_merge * (double)n0[sb]) or_union(gpar, sa, sb);
+    k = k2;
+  }
+  /* 4. labels */
+  int64_t *minidx = (int64_t *)malloc((size_t)nh * sizeof(int64_t));
+  for (int64_t i = 0; i < nh; ++i) minidx[i] = INT64_MAX;
+  int64_t *gslot = (int64_t *)malloc((size_t)nh * sizeof(int64_t));
+  for (int64_t i = 0; i < nh; ++i) {
+    gslot[i] = -1;
+    if (grown[i] < 0) continue;
+    gslot[i] = or_find(gpar, or_slot(members, nh, grown[i]));
+    if (members[i] < minidx[gslot[i]]) minidx[gslot[i]] = members[i];
+  }
+  for (int64_t i = 0; i < nh; ++i) out[i] = gslot[i] >= 0 ? (int32_t)minidx[gslot[i]] : -1;
+  free(gslot); free(minidx); free(gpar); free(ab); free(n0); free(grown);
+  free(bestn); free(best); free(cg); free(parent); free(e); free(cand);
+  return 0;
+}
+
 /* ------------------------------------------------------- field 6DFOF (Sec. 2.1) */
 
 /* Field halos (Sec. 2.1, Eq. fof6d): every 3DFOF group of >= nmin members is split by a
