@@ -202,6 +202,40 @@ vr_status vr_find_substructure(vr_ctx *ctx, const int32_t *pos, const float *vel
                                float *ell, int32_t *label6, double *halo_stats, int64_t *nhalo,
                                void *ws, size_t ws_bytes, void *stream);
 
+/* Two-stage linking (Sec. 2.2, "Linking particles": conservative criteria find the
+ * candidate substructures; relaxed criteria then link previously untagged particles to
+ * them, and substructures are joined only when the new connections exceed f_merge times
+ * the original size of either). The relaxed pass takes, inside every halo whose
+ * VR_H_SEARCHED is set, the candidates ell >= ell_th / gamma_ell plus every particle
+ * already in a group, and the predicate of vr_fof6d with lx2 gamma_x^2 (evaluated as
+ * (lx2 gamma_x) gamma_x), V_r gamma_vr and Theta_op gamma_theta (lv2 and frame
+ * unchanged). In this order:
+ *  1. the untagged candidates form connected components under the relaxed links among
+ *     themselves;
+ *  2. a component joins the group with the most relaxed links between its members and
+ *     the group's (ties: the smaller label); with no such link it stays untagged;
+ *  3. two grown groups A, B are joined iff the relaxed links between their members
+ *     number more than f_merge N_o(A) or f_merge N_o(B), N_o the size on input; joins
+ *     are transitive;
+ *  4. each final group is labelled with its minimum particle index.
+ * Table A1 defaults (vr_grow_params_default): gamma_ell 1, gamma_x 2, gamma_vr 1,
+ * gamma_theta 1; f_merge 0.25 (Sec. 2.2). */
+typedef struct {
+  double gamma_ell, gamma_x, gamma_vr, gamma_theta, f_merge;
+} vr_grow_params;
+
+void vr_grow_params_default(vr_grow_params *g);
+
+/*   ell, label, halo_params, nhalo  as for vr_fof6d
+ *   label6  int32 [n] in/out: the stage-1 labels of vr_fof6d in, the grown labels out
+ * Errors: VR_ERR_INVALID_ARG for a factor <= 0, f_merge < 0 or gamma_theta Theta_op >=
+ * pi/2; VR_ERR_UNSUPPORTED if a link-count table overflows (more distinct (component,
+ * group) or (group, group) pairs than n). This call synchronises `stream`. */
+vr_status vr_grow_groups(vr_ctx *ctx, const int32_t *pos, const float *vel, const float *ell,
+                         int64_t n, const int32_t *label, const double *halo_params,
+                         int64_t nhalo, const vr_params *p, const vr_grow_params *gp,
+                         int32_t *label6, void *ws, size_t ws_bytes, void *stream);
+
 /* Cleaning of outlier groups (Sec. 2.2, "Cleaning the catalogue", Eq. ellsig). A group
  * of N particles (equal labels >= 0 in label6) is significant iff
  *   <ell> >= ell_bar(p->ell_th) (1 + beta/sqrt(N)),

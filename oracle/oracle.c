@@ -1066,13 +1066,17 @@ int or_grow_halo(const int64_t *upos, const float *vel, const int32_t *members, 
   const double vr2 = vr * vr, cos2 = ct * ct;
   uint8_t *cand = (uint8_t *)malloc((size_t)nh);
   for (int64_t i = 0; i < nh; ++i) cand[i] = lab1[i] >= 0 || ell[i] >= thr;
-  /* the relaxed links, once */
+  /* the relaxed links, once (over the candidates, in member order) */
+  int64_t nc = 0;
+  int64_t *ci = (int64_t *)malloc((size_t)nh * sizeof(int64_t));
+  for (int64_t i = 0; i < nh; ++i)
+    if (cand[i]) ci[nc++] = i;
   int64_t ne = 0, cap = 1024;
   or_pair *e = (or_pair *)malloc((size_t)cap * sizeof(or_pair));
-  for (int64_t i = 0; i < nh; ++i) {
-    if (!cand[i]) continue;
-    for (int64_t j = i + 1; j < nh; ++j) {
-      if (!cand[j]) continue;
+  for (int64_t x = 0; x < nc; ++x) {
+    const int64_t i = ci[x];
+    for (int64_t y = x + 1; y < nc; ++y) {
+      const int64_t j = ci[y];
       int64_t d2 = 0;
       for (int c = 0; c < 3; ++c) {
         int64_t d = upos[3 * i + c] - upos[3 * j + c];
@@ -1163,7 +1167,7 @@ int or_grow_halo(const int64_t *upos, const float *vel, const int32_t *members, 
   }
   for (int64_t i = 0; i < nh; ++i) out[i] = gslot[i] >= 0 ? (int32_t)minidx[gslot[i]] : -1;
   free(gslot); free(minidx); free(gpar); free(ab); free(n0); free(grown);
-  free(bestn); free(best); free(cg); free(parent); free(e); free(cand);
+  free(bestn); free(best); free(cg); free(parent); free(e); free(ci); free(cand);
   return 0;
 }
 

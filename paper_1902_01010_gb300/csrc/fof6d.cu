@@ -25,10 +25,12 @@ namespace vr {
 
 namespace {
 
+// Candidates: members of linked halos with ell >= ell_th (every member when ell is NULL),
+// and every member already in a group when `tag` is given.
 __global__ void k_cand_flags(const uint32_t *__restrict__ hid, int64_t nhp,
                              const float4 *__restrict__ v, const float *__restrict__ ell,
                              const double *__restrict__ hp, int64_t nhalo, double ell_th,
-                             uint32_t *__restrict__ flag) {
+                             const int32_t *__restrict__ tag, uint32_t *__restrict__ flag) {
   int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (m > nhp) return;
   if (m == nhp) {
@@ -38,8 +40,8 @@ __global__ void k_cand_flags(const uint32_t *__restrict__ hid, int64_t nhp,
   uint32_t h = hid[m];
   bool c = h < (uint64_t)nhalo && hp[(int64_t)h * VR_HALO_COLS + VR_H_SEARCHED] != 0.0;
   if (c && ell) {
-    float e = ell[__float_as_int(v[m].w)];
-    c = (double)e >= ell_th;  // false for NaN
+    const int pi = __float_as_int(v[m].w);
+    c = (double)ell[pi] >= ell_th || (tag && tag[pi] >= 0);  // false for NaN
   }
   flag[m] = c ? 1u : 0u;
 }
@@ -143,6 +145,43 @@ __device__ __forceinline__ bool link6(long long dx2, float4 a, float4 b, const L
 // [1 - 1e-5, 1 + 1e-5] decides the FP64 comparison too; pairs inside that band, and every
 // pair when V_r / Theta_op are on, take the exact FP64 path. The FP32 route is used only
 // when lx2 and lv2 are normal FP32 numbers.
+//
+// The same walk serves the relaxed pass of the two-stage linking (MODE > 0, lx2 scaled
+// by gamma_x^2): MODE 1 unites linked pairs of untagged candidates, MODE 2 counts links
+// between an untagged candidate's component and a tagged candidate's group, MODE 3
+// counts links between candidates of two different grown groups (counts in a hash table
+// keyed by the pair).
+enum { kLink = 0, kUntagged = 1, kToGroup = 2, kCross = 3 };
+
+struct GrowArgs {
+  double gx;             // gamma_x
+  const int *tag;        // [nc] stage-1 label of the candidate's particle, -1 untagged
+  const int *croot;      // [nc] root of the candidate's untagged component
+  const int *grown;      // [nc] grown group label, -1 none
+  u64 *hkey;             // hash table keys (kEmptyKey = free)
+  uint32_t *hcnt;        // hash table counts
+  u64 hmask;             // capacity - 1 (a power of two)
+  DevStatus *st;
+};
+
+constexpr u64 kEmptyKey = ~0ULL;
+
+// Adds one to the count of `key` (open addressing, linear probing, bounded).
+__device__ __forceinline__ void hash_add(const GrowArgs &G, u64 key) {
+  const u64 h0 = (key * 0x9E3779B97F4A7C15ull) >> 16;
+  for (u64 probe = 0; probe < 4096; ++probe) {
+    const u64 i = (h0 + probe) & G.hmask;
+    u64 k = __ldcg(G.hkey + i);
+    if (k == kEmptyKey) k = atomicCAS((unsigned long long *)(G.hkey + i), kEmptyKey, key);
+    if (k == kEmptyKey || k == key) {
+      atomicAdd(G.hcnt + i, 1u);
+      return;
+    }
+  }
+  raise_error(G.st, VR_ERR_UNSUPPORTED, 5);
+}
+
+template <int MODE>
 __global__ void __launch_bounds__(128) k_link6(const uint32_t *__restrict__ toff,
                                                const uint32_t *__restrict__ coff,
                                                const uint32_t *__restrict__ thalo, int64_t t0,
@@ -151,10 +190,13 @@ __global__ void __launch_bounds__(128) k_link6(const uint32_t *__restrict__ toff
                                                const int4 *__restrict__ tmin,
                                                const int4 *__restrict__ tmax,
                                                const double *__restrict__ hp, double vr2,
-                                               double cos2, int use_lv, int use_vt, int *parent) {
+                                               double cos2, int use_lv, int use_vt, int *parent,
+                                               GrowArgs G) {
   __shared__ int4 s_u[4][32];
   __shared__ float4 s_v[4][32];
   __shared__ int s_r[4][32];
+  __shared__ int s_x[4][32];
+  __shared__ int s_y[4][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const unsigned FULL = 0xffffffffu;
   const int64_t ti = t0 + (int64_t)blockIdx.x * (blockDim.x / 32) + w;  // tiles [t0, t1)
@@ -167,6 +209,7 @@ __global__ void __launch_bounds__(128) k_link6(const uint32_t *__restrict__ toff
   L.vf0 = row[VR_H_VFX];
   L.vf1 = row[VR_H_VFY];
   L.vf2 = row[VR_H_VFZ];
+  if (MODE != kLink) L.lx2 = __dmul_rn(__dmul_rn(L.lx2, G.gx), G.gx);
   L.vr2 = vr2;
   L.cos2 = cos2;
   L.use_lv = use_lv;
@@ -181,6 +224,8 @@ __global__ void __launch_bounds__(128) k_link6(const uint32_t *__restrict__ toff
   const int4 pa = cu[va ? ia + lane : ia];
   const float4 qa = cv[va ? ia + lane : ia];
   const int4 alo = tmin[ti], ahi = tmax[ti];
+  const int xa = MODE == kLink || !va ? -1 : (MODE == kCross ? G.grown[ia + lane] : G.tag[ia + lane]);
+  const int ya = MODE == kToGroup && va ? G.croot[ia + lane] : -1;
   // the spatial term alone must be < 1: dx2 < lx2
   for (uint32_t base = (uint32_t)ti; base < th1; base += 32) {
     const uint32_t tj = base + lane;
@@ -201,19 +246,28 @@ __global__ void __launch_bounds__(128) k_link6(const uint32_t *__restrict__ toff
       // current roots of both tiles' members: a tile pair whose members all share one set
       // has nothing left to link (sets only ever merge, so an equal pair of roots, even
       // stale ones, proves the two members connected)
-      const int ra = va ? uf_find(parent, (int)(ia + lane)) : -1;
-      const int rb = (uint32_t)lane < nbb ? uf_find(parent, (int)(ib + lane)) : -1;
+      constexpr bool kUnion = MODE == kLink || MODE == kUntagged;
+      const int ra = kUnion && va ? uf_find(parent, (int)(ia + lane)) : -1;
+      const int rb = kUnion && (uint32_t)lane < nbb ? uf_find(parent, (int)(ib + lane)) : -1;
       if ((uint32_t)lane < nbb) {
         s_u[w][lane] = cu[ib + lane];
         s_v[w][lane] = cv[ib + lane];
         s_r[w][lane] = rb;
+        if (MODE != kLink) s_x[w][lane] = MODE == kCross ? G.grown[ib + lane] : G.tag[ib + lane];
+        if (MODE == kToGroup) s_y[w][lane] = G.croot[ib + lane];
       }
-      const int r0 = __shfl_sync(FULL, ra, 0);
-      if (__all_sync(FULL, (!va || ra == r0) && ((uint32_t)lane >= nbb || rb == r0))) continue;
+      if (kUnion) {
+        const int r0 = __shfl_sync(FULL, ra, 0);
+        if (__all_sync(FULL, (!va || ra == r0) && ((uint32_t)lane >= nbb || rb == r0))) continue;
+      }
       __syncwarp();
       if (!va) continue;
       int rk = ra;  // a member of this lane's set, for the connected-pair skip below
       for (uint32_t k = tb == (uint32_t)ti ? (uint32_t)lane + 1 : 0; k < nbb; ++k) {
+        // pairs this mode has no use for, before any arithmetic
+        if (MODE == kUntagged && (xa >= 0 || s_x[w][k] >= 0)) continue;
+        if (MODE == kToGroup && (xa < 0) == (s_x[w][k] < 0)) continue;
+        if (MODE == kCross && (xa < 0 || s_x[w][k] < 0 || xa == s_x[w][k])) continue;
         const int4 p = s_u[w][k];
         const float4 q = s_v[w][k];
         const long long dx = (long long)pa.x - p.x, dy = (long long)pa.y - p.y,
@@ -233,9 +287,19 @@ __global__ void __launch_bounds__(128) k_link6(const uint32_t *__restrict__ toff
         } else {
           link = link6(dx2, qa, q, L);
         }
-        if (link && s_r[w][k] != rk) {
-          uf_unite(parent, (int)(ia + lane), (int)(ib + k));
-          rk = min(rk, s_r[w][k]);  // now in this lane's set
+        if (!link) continue;
+        if (kUnion) {
+          if (s_r[w][k] != rk) {
+            uf_unite(parent, (int)(ia + lane), (int)(ib + k));
+            rk = min(rk, s_r[w][k]);  // now in this lane's set
+          }
+        } else if (MODE == kToGroup) {
+          const u64 c = (u64)(uint32_t)(xa < 0 ? ya : s_y[w][k]);
+          const u64 g = (u64)(uint32_t)(xa < 0 ? s_x[w][k] : xa);
+          hash_add(G, (c << 32) | g);
+        } else {
+          const int b = s_x[w][k];
+          hash_add(G, ((u64)(uint32_t)min(xa, b) << 32) | (u64)(uint32_t)max(xa, b));
         }
       }
     }
@@ -286,6 +350,13 @@ __global__ void k_fill_i32(int32_t *__restrict__ a, int64_t n, int32_t val) {
   if (i < n) a[i] = val;
 }
 
+// Hash table capacity for the two-stage counts: a power of two >= n / 2.
+int64_t grow_table_cap(int64_t n) {
+  int64_t c = 1024;
+  while (c < n / 2) c <<= 1;
+  return c;
+}
+
 }  // namespace
 
 size_t fof6d_bytes(int64_t n, int nmin) {
@@ -323,77 +394,263 @@ vr_status fill_i32(vr_ctx *ctx, int32_t *a, int64_t n, int32_t val, cudaStream_t
   return VR_OK;
 }
 
+namespace {
+
+// Candidates compacted per halo in slot order, with their tiles and tile boxes.
+struct Cands {
+  uint32_t nc = 0, ntiles = 0;
+  int4 *cu;
+  float4 *cv;
+  uint32_t *coff, *toff, *thalo;
+  int4 *tmin, *tmax;
+  int *parent, *minidx, *size;
+};
+
+vr_status prep_cands(vr_ctx *ctx, const HaloSeg &g, int nmin, Arena &ar, const float *ell,
+                     double ell_thr, const int32_t *tag, const double *hp, int64_t nhalo,
+                     cudaStream_t s, Cands *C) {
+  const int64_t H = g.H, nhp = g.NHP;
+  int64_t hmax = g.n / (nmin > 0 ? nmin : 1) + 2;
+  int64_t tmaxn = g.n / 32 + hmax + 2;
+  uint32_t *flag = ar.take<uint32_t>(g.n + 1);
+  C->cu = ar.take<int4>(g.n);
+  C->cv = ar.take<float4>(g.n);
+  uint32_t *chid = ar.take<uint32_t>(g.n);
+  C->coff = ar.take<uint32_t>(hmax + 1);
+  C->toff = ar.take<uint32_t>(hmax + 1);
+  C->thalo = ar.take<uint32_t>(tmaxn);
+  C->tmin = ar.take<int4>(tmaxn);
+  C->tmax = ar.take<int4>(tmaxn);
+  C->parent = ar.take<int>(g.n);
+  C->minidx = ar.take<int>(g.n);
+  C->size = ar.take<int>(g.n);
+  void *scr = ar.take<char>(scan_scratch_bytes<uint32_t>(g.n + 1));
+  if (!ar.ok()) return set_error(ctx, VR_ERR_WORKSPACE_TOO_SMALL, "workspace too small");
+  const int T = 256;
+  k_cand_flags<<<grid_for(nhp + 1, T), T, 0, s>>>(g.hid, nhp, g.v, ell, hp, nhalo, ell_thr, tag, flag);
+  VR_LAUNCHED(ctx, "k_cand_flags");
+  VR_CUDA(ctx, exclusive_scan<uint32_t>(flag, flag, nhp + 1, scr, s));
+  k_cand_compact<<<grid_for(nhp, T), T, 0, s>>>(flag, g.hid, nhp, g.u, g.v, C->cu, C->cv, chid);
+  VR_LAUNCHED(ctx, "k_cand_compact");
+  k_cand_halos<<<grid_for(H + 1, T), T, 0, s>>>(g.hoff, flag, H, C->coff, C->toff);
+  VR_LAUNCHED(ctx, "k_cand_halos");
+  VR_CUDA(ctx, exclusive_scan<uint32_t>(C->toff, C->toff, H + 1, scr, s));
+  VR_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned + 35, flag + nhp, sizeof(uint32_t),
+                               cudaMemcpyDeviceToHost, s));
+  VR_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned + 36, C->toff + H, sizeof(uint32_t),
+                               cudaMemcpyDeviceToHost, s));
+  VR_CUDA(ctx, cudaStreamSynchronize(s));
+  memcpy(&C->nc, ctx->h_pinned + 35, 4);
+  memcpy(&C->ntiles, ctx->h_pinned + 36, 4);
+  if (C->nc == 0) return VR_OK;
+  k_tile_fill<<<grid_for(H, T), T, 0, s>>>(C->toff, H, C->thalo);
+  VR_LAUNCHED(ctx, "k_tile_fill");
+  k_tile_boxes<<<grid_for(C->ntiles, T), T, 0, s>>>(C->toff, C->coff, C->thalo, C->ntiles, C->cu,
+                                                    C->tmin, C->tmax);
+  VR_LAUNCHED(ctx, "k_tile_boxes");
+  k_cand_init<<<grid_for(C->nc, T), T, 0, s>>>(C->nc, C->parent, C->minidx, C->size);
+  VR_LAUNCHED(ctx, "k_cand_init");
+  return VR_OK;
+}
+
+// ------------------------------------------------------- two-stage linking kernels
+
+// Stage-1 label of each candidate and stage-1 group sizes (indexed by label).
+__global__ void k_grow_tags(const float4 *__restrict__ cv, int64_t nc,
+                            const int32_t *__restrict__ label6, int *__restrict__ tag,
+                            int *__restrict__ n0) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  const int t = label6[__float_as_int(cv[c].w)];
+  tag[c] = t;
+  if (t >= 0) atomicAdd(&n0[t], 1);
+}
+
+__global__ void k_grow_roots(int *parent, int64_t nc, int *__restrict__ croot) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < nc) croot[c] = uf_find(parent, (int)c);
+}
+
+__global__ void k_hash_clear(u64 *__restrict__ key, uint32_t *__restrict__ cnt, int64_t cap) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cap) return;
+  key[i] = kEmptyKey;
+  cnt[i] = 0;
+}
+
+// Per untagged component: the group with the most links (ties: the smaller label), as
+// (count << 32 | ~label) maximised.
+__global__ void k_grow_attach(const u64 *__restrict__ key, const uint32_t *__restrict__ cnt,
+                              int64_t cap, unsigned long long *__restrict__ best) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cap || key[i] == kEmptyKey) return;
+  const uint32_t c = (uint32_t)(key[i] >> 32), g = (uint32_t)key[i];
+  atomicMax(&best[c], ((unsigned long long)cnt[i] << 32) | (unsigned long long)(~g));
+}
+
+__global__ void k_grow_label(const int *__restrict__ tag, const int *__restrict__ croot,
+                             const unsigned long long *__restrict__ best, int64_t nc,
+                             int *__restrict__ grown) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  if (tag[c] >= 0) {
+    grown[c] = tag[c];
+    return;
+  }
+  const unsigned long long b = best[croot[c]];
+  grown[c] = b ? (int)(~(uint32_t)b) : -1;
+}
+
+__global__ void k_iota(int *__restrict__ a, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = (int)i;
+}
+
+// Joins of grown groups A < B with more than f_merge N_o links between them (either).
+__global__ void k_grow_merge(const u64 *__restrict__ key, const uint32_t *__restrict__ cnt,
+                             int64_t cap, const int *__restrict__ n0, double f_merge, int *gpar) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cap || key[i] == kEmptyKey) return;
+  const int a = (int)(key[i] >> 32), b = (int)(uint32_t)key[i];
+  const double c = (double)cnt[i];
+  if (c > f_merge * (double)n0[a] || c > f_merge * (double)n0[b]) uf_unite(gpar, a, b);
+}
+
+__global__ void k_grow_min(int *gpar, const int *__restrict__ grown, const float4 *__restrict__ cv,
+                           int64_t nc, int *__restrict__ minidx) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc || grown[c] < 0) return;
+  atomicMin(&minidx[uf_find(gpar, grown[c])], __float_as_int(cv[c].w));
+}
+
+__global__ void k_grow_out(int *gpar, const int *__restrict__ grown, const float4 *__restrict__ cv,
+                           int64_t nc, const int *__restrict__ minidx, int32_t *__restrict__ label6) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc || grown[c] < 0) return;
+  label6[__float_as_int(cv[c].w)] = minidx[uf_find(gpar, grown[c])];
+}
+
+}  // namespace
+
 vr_status run_fof6d(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Arena &ar,
                     const float *ell, const double *hp, int64_t nhalo, int32_t *label6,
                     cudaStream_t s, bool plain) {
   if (g.H == 0) return VR_OK;
-  const int64_t H = g.H, nhp = g.NHP;
-  int64_t hmax = g.n / (p->nmin > 0 ? p->nmin : 1) + 2;
-  int64_t tmaxn = g.n / 32 + hmax + 2;
-  uint32_t *flag = ar.take<uint32_t>(g.n + 1);
-  int4 *cu = ar.take<int4>(g.n);
-  float4 *cv = ar.take<float4>(g.n);
-  uint32_t *chid = ar.take<uint32_t>(g.n);
-  uint32_t *coff = ar.take<uint32_t>(hmax + 1);
-  uint32_t *toff = ar.take<uint32_t>(hmax + 1);
-  uint32_t *thalo = ar.take<uint32_t>(tmaxn);
-  int4 *tmin = ar.take<int4>(tmaxn);
-  int4 *tmax = ar.take<int4>(tmaxn);
-  int *parent = ar.take<int>(g.n);
-  int *minidx = ar.take<int>(g.n);
-  int *size = ar.take<int>(g.n);
-  void *scr = ar.take<char>(scan_scratch_bytes<uint32_t>(g.n + 1));
-  if (!ar.ok()) return set_error(ctx, VR_ERR_WORKSPACE_TOO_SMALL, "workspace too small");
+  const int64_t H = g.H;
+  Cands C;
+  vr_status st = prep_cands(ctx, g, p->nmin, ar, ell, p->ell_th, nullptr, hp, nhalo, s, &C);
+  if (st != VR_OK || C.nc == 0) return st;
   const int T = 256;
-  k_cand_flags<<<grid_for(nhp + 1, T), T, 0, s>>>(g.hid, nhp, g.v, ell, hp, nhalo, p->ell_th, flag);
-  VR_LAUNCHED(ctx, "k_cand_flags");
-  VR_CUDA(ctx, exclusive_scan<uint32_t>(flag, flag, nhp + 1, scr, s));
-  k_cand_compact<<<grid_for(nhp, T), T, 0, s>>>(flag, g.hid, nhp, g.u, g.v, cu, cv, chid);
-  VR_LAUNCHED(ctx, "k_cand_compact");
-  k_cand_halos<<<grid_for(H + 1, T), T, 0, s>>>(g.hoff, flag, H, coff, toff);
-  VR_LAUNCHED(ctx, "k_cand_halos");
-  VR_CUDA(ctx, exclusive_scan<uint32_t>(toff, toff, H + 1, scr, s));
-  VR_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned + 35, flag + nhp, sizeof(uint32_t),
-                               cudaMemcpyDeviceToHost, s));
-  VR_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned + 36, toff + H, sizeof(uint32_t),
-                               cudaMemcpyDeviceToHost, s));
-  VR_CUDA(ctx, cudaStreamSynchronize(s));
-  uint32_t nc = 0, ntiles = 0;
-  memcpy(&nc, ctx->h_pinned + 35, 4);
-  memcpy(&ntiles, ctx->h_pinned + 36, 4);
-  if (nc == 0) return VR_OK;
-  k_tile_fill<<<grid_for(H, T), T, 0, s>>>(toff, H, thalo);
-  VR_LAUNCHED(ctx, "k_tile_fill");
-  k_tile_boxes<<<grid_for(ntiles, T), T, 0, s>>>(toff, coff, thalo, ntiles, cu, tmin, tmax);
-  VR_LAUNCHED(ctx, "k_tile_boxes");
-  k_cand_init<<<grid_for(nc, T), T, 0, s>>>(nc, parent, minidx, size);
-  VR_LAUNCHED(ctx, "k_cand_init");
   const double vr2 = p->v_ratio * p->v_ratio;
   const double ct = cos(p->theta_op);
   const double cos2 = ct * ct;
+  GrowArgs G{};
   if (plain) {  // one launch per halo
     std::vector<uint32_t> th(H + 1);
-    VR_CUDA(ctx, cudaMemcpyAsync(th.data(), toff, (H + 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    VR_CUDA(ctx, cudaMemcpyAsync(th.data(), C.toff, (H + 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     VR_CUDA(ctx, cudaStreamSynchronize(s));
     for (int64_t h = 0; h < H; ++h) {
       if (th[h + 1] == th[h]) continue;
-      k_link6<<<grid_for(th[h + 1] - th[h], 4), 128, 0, s>>>(toff, coff, thalo, th[h], th[h + 1], cu,
-                                                              cv, tmin, tmax, hp, vr2, cos2,
-                                                              p->use_lv, p->use_vr_theta, parent);
+      k_link6<kLink><<<grid_for(th[h + 1] - th[h], 4), 128, 0, s>>>(
+          C.toff, C.coff, C.thalo, th[h], th[h + 1], C.cu, C.cv, C.tmin, C.tmax, hp, vr2, cos2,
+          p->use_lv, p->use_vr_theta, C.parent, G);
       VR_LAUNCHED(ctx, "k_link6");
     }
   } else {
-    VR_TIMED(ctx, "link6", s, k_link6<<<grid_for(ntiles, 4), 128, 0, s>>>(toff, coff, thalo, 0, ntiles, cu, cv, tmin,
-                                                                       tmax, hp, vr2, cos2, p->use_lv,
-                                                                       p->use_vr_theta, parent));
+    VR_TIMED(ctx, "link6", s, k_link6<kLink><<<grid_for(C.ntiles, 4), 128, 0, s>>>(
+        C.toff, C.coff, C.thalo, 0, C.ntiles, C.cu, C.cv, C.tmin, C.tmax, hp, vr2, cos2,
+        p->use_lv, p->use_vr_theta, C.parent, G));
     VR_LAUNCHED(ctx, "k_link6");
   }
-  k_cand_roots<<<grid_for(nc, T), T, 0, s>>>(parent, cv, nc, minidx, size);
+  k_cand_roots<<<grid_for(C.nc, T), T, 0, s>>>(C.parent, C.cv, C.nc, C.minidx, C.size);
   VR_LAUNCHED(ctx, "k_cand_roots");
-  k_cand_label<<<grid_for(nc, T), T, 0, s>>>(parent, cv, nc, minidx, size, p->nmin, label6);
+  k_cand_label<<<grid_for(C.nc, T), T, 0, s>>>(C.parent, C.cv, C.nc, C.minidx, C.size, p->nmin, label6);
   VR_LAUNCHED(ctx, "k_cand_label");
-  (void)chid;
   return VR_OK;
+}
+
+vr_status run_grow(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, const vr_grow_params *gp,
+                   Arena &ar, const float *ell, const double *hp, int64_t nhalo, int32_t *label6,
+                   cudaStream_t s) {
+  if (g.H == 0) return VR_OK;
+  Cands C;
+  vr_status st = prep_cands(ctx, g, p->nmin, ar, ell, p->ell_th / gp->gamma_ell, label6, hp,
+                            nhalo, s, &C);
+  if (st != VR_OK) return st;
+  const int64_t n = g.n, tcap = grow_table_cap(n);
+  int *tag = ar.take<int>(n);
+  int *croot = ar.take<int>(n);
+  int *grown = ar.take<int>(n);
+  unsigned long long *best = ar.take<unsigned long long>(n);
+  int *n0 = ar.take<int>(n);
+  int *gpar = ar.take<int>(n);
+  int *minidx = ar.take<int>(n);
+  u64 *hkey = ar.take<u64>(tcap);
+  uint32_t *hcnt = ar.take<uint32_t>(tcap);
+  if (!ar.ok()) return set_error(ctx, VR_ERR_WORKSPACE_TOO_SMALL, "workspace too small");
+  const int64_t nc = C.nc;
+  if (nc == 0) return VR_OK;
+  int64_t cap = 1024;  // table in use: a power of two >= 2 nc
+  while (cap < 2 * nc && cap < tcap) cap <<= 1;
+  const int T = 256;
+  VR_CUDA(ctx, cudaMemsetAsync(n0, 0, n * sizeof(int), s));
+  VR_CUDA(ctx, cudaMemsetAsync(best, 0, nc * sizeof(unsigned long long), s));
+  k_grow_tags<<<grid_for(nc, T), T, 0, s>>>(C.cv, nc, label6, tag, n0);
+  VR_LAUNCHED(ctx, "k_grow_tags");
+  const double vr = p->v_ratio * gp->gamma_vr, ct = cos(p->theta_op * gp->gamma_theta);
+  const double vr2 = vr * vr, cos2 = ct * ct;
+  GrowArgs G{gp->gamma_x, tag, croot, grown, hkey, hcnt, (u64)(cap - 1), ctx->d_status};
+  auto pass = [&](auto kernel) {
+    kernel<<<grid_for(C.ntiles, 4), 128, 0, s>>>(C.toff, C.coff, C.thalo, 0, C.ntiles, C.cu, C.cv,
+                                                 C.tmin, C.tmax, hp, vr2, cos2, p->use_lv,
+                                                 p->use_vr_theta, C.parent, G);
+  };
+  // 1. components of the untagged candidates
+  pass(k_link6<kUntagged>);
+  VR_LAUNCHED(ctx, "k_link6<untagged>");
+  k_grow_roots<<<grid_for(nc, T), T, 0, s>>>(C.parent, nc, croot);
+  VR_LAUNCHED(ctx, "k_grow_roots");
+  // 2. links from components to groups; each component joins its most linked group
+  k_hash_clear<<<grid_for(cap, T), T, 0, s>>>(hkey, hcnt, cap);
+  VR_LAUNCHED(ctx, "k_hash_clear");
+  pass(k_link6<kToGroup>);
+  VR_LAUNCHED(ctx, "k_link6<to_group>");
+  k_grow_attach<<<grid_for(cap, T), T, 0, s>>>(hkey, hcnt, cap, best);
+  VR_LAUNCHED(ctx, "k_grow_attach");
+  k_grow_label<<<grid_for(nc, T), T, 0, s>>>(tag, croot, best, nc, grown);
+  VR_LAUNCHED(ctx, "k_grow_label");
+  // 3. links between grown groups; joins above the merge threshold
+  k_hash_clear<<<grid_for(cap, T), T, 0, s>>>(hkey, hcnt, cap);
+  VR_LAUNCHED(ctx, "k_hash_clear");
+  pass(k_link6<kCross>);
+  VR_LAUNCHED(ctx, "k_link6<cross>");
+  k_iota<<<grid_for(n, T), T, 0, s>>>(gpar, n);
+  VR_LAUNCHED(ctx, "k_iota");
+  k_grow_merge<<<grid_for(cap, T), T, 0, s>>>(hkey, hcnt, cap, n0, gp->f_merge, gpar);
+  VR_LAUNCHED(ctx, "k_grow_merge");
+  // 4. labels: minimum particle index of each final group
+  k_fill_i32<<<grid_for(n, T), T, 0, s>>>(minidx, n, 0x7fffffff);
+  VR_LAUNCHED(ctx, "k_fill_i32");
+  k_grow_min<<<grid_for(nc, T), T, 0, s>>>(gpar, grown, C.cv, nc, minidx);
+  VR_LAUNCHED(ctx, "k_grow_min");
+  k_grow_out<<<grid_for(nc, T), T, 0, s>>>(gpar, grown, C.cv, nc, minidx, label6);
+  VR_LAUNCHED(ctx, "k_grow_out");
+  return VR_OK;
+}
+
+size_t grow_bytes(int64_t n, int nmin) {
+  Arena ar;
+  ar.off = fof6d_bytes(n, nmin);
+  ar.take<int>(n);                 // tag
+  ar.take<int>(n);                 // croot
+  ar.take<int>(n);                 // grown
+  ar.take<unsigned long long>(n);  // best
+  ar.take<int>(n);                 // n0
+  ar.take<int>(n);                 // gpar
+  ar.take<int>(n);                 // minidx
+  ar.take<u64>(grow_table_cap(n));
+  ar.take<uint32_t>(grow_table_cap(n));
+  return ar.off;
 }
 
 }  // namespace vr

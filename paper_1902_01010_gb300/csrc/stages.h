@@ -23,6 +23,11 @@ vr_status field_lengths(vr_ctx *ctx, int64_t H, double lx2, double alpha_v, doub
 vr_status run_fof6d(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Arena &ar,
                     const float *ell, const double *hp, int64_t nhalo, int32_t *label6,
                     cudaStream_t s, bool plain = false);
+size_t grow_bytes(int64_t n, int nmin);
+// Two-stage linking: relaxed growth of the stage-1 groups in label6 (in/out).
+vr_status run_grow(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, const vr_grow_params *gp,
+                   Arena &ar, const float *ell, const double *hp, int64_t nhalo, int32_t *label6,
+                   cudaStream_t s);
 size_t clean_bytes(int64_t n);
 // Significance cleaning of groups (Eq. ellsig); synchronises the stream.
 vr_status run_clean(vr_ctx *ctx, const float *ell, int64_t n, const vr_params *p, double beta,

@@ -14,8 +14,9 @@ size_t ws_substructure(int64_t n, const vr_params *p) {
   size_t a = velden_bytes(n, p->nmin), b = background_bytes(n, p), c = fof6d_bytes(n, p->nmin);
   size_t m = a > b ? a : b;
   m = m > c ? m : c;
-  const size_t cl = clean_bytes(n);
+  const size_t cl = clean_bytes(n), gr = grow_bytes(n, p->nmin);
   m = m > cl ? m : cl;
+  m = m > gr ? m : gr;
   return halo_seg_bytes(n, p->nmin) + m + 4096;
 }
 
@@ -133,6 +134,41 @@ vr_status vr_fof6d_field(vr_ctx *ctx, const int32_t *pos, const float *vel, int6
   q.use_vr_theta = 0;
   if ((st = run_fof6d(ctx, g, &q, ar, nullptr, halo_stats, g.H, label6, s)) != VR_OK) return st;
   if (nhalo) *nhalo = g.H;
+  return read_status(ctx, s, nullptr);
+}
+
+void vr_grow_params_default(vr_grow_params *g) {
+  if (!g) return;
+  g->gamma_ell = 1.0;
+  g->gamma_x = 2.0;
+  g->gamma_vr = 1.0;
+  g->gamma_theta = 1.0;
+  g->f_merge = 0.25;
+}
+
+vr_status vr_grow_groups(vr_ctx *ctx, const int32_t *pos, const float *vel, const float *ell,
+                         int64_t n, const int32_t *label, const double *halo_params,
+                         int64_t nhalo, const vr_params *p, const vr_grow_params *gp,
+                         int32_t *label6, void *ws, size_t ws_bytes, void *stream) {
+  if (!ctx) return VR_ERR_INVALID_ARG;
+  vr_status st = common_checks(ctx, n, p);
+  if (st != VR_OK) return st;
+  if (n == 0) return VR_OK;
+  if (!pos || !vel || !ell || !label || !halo_params || !gp || !label6 || !ws)
+    return set_error(ctx, VR_ERR_INVALID_ARG, "NULL pointer");
+  if (!(gp->gamma_ell > 0.0) || !(gp->gamma_x > 0.0) || !(gp->gamma_vr > 0.0) ||
+      !(gp->gamma_theta > 0.0) || !(gp->f_merge >= 0.0))
+    return set_error(ctx, VR_ERR_INVALID_ARG, "gamma factors must be > 0 and f_merge >= 0");
+  if (!(p->theta_op * gp->gamma_theta < 1.5707963267948966))
+    return set_error(ctx, VR_ERR_INVALID_ARG, "gamma_theta * theta_op must be < pi/2");
+  cudaStream_t s = (cudaStream_t)stream;
+  Arena ar(ws, ws_bytes);
+  HaloSeg g;
+  if ((st = build_halos(ctx, pos, vel, n, label, p->nmin, p->nse, ar, s, &g)) != VR_OK) return st;
+  if (nhalo != g.H)
+    return set_error(ctx, VR_ERR_INVALID_ARG, "nhalo = %lld but the labels define %lld halos",
+                     (long long)nhalo, (long long)g.H);
+  if ((st = run_grow(ctx, g, p, gp, ar, ell, halo_params, nhalo, label6, s)) != VR_OK) return st;
   return read_status(ctx, s, nullptr);
 }
 

@@ -138,6 +138,7 @@ vr_status read_status(vr_ctx *ctx, cudaStream_t s, DevStatus *out) {
       case 1: what = "halo spans half the box or more, or holds more than 2^22 particles"; break;
       case 2: what = "k-NN candidate search exceeded its bound"; break;
       case 3: what = "background cell tree exceeded its depth bound"; break;
+      case 5: what = "link-count table of the two-stage linking is full"; break;
       default: break;
     }
     // clear for the next call

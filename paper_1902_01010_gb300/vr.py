@@ -25,7 +25,8 @@ H_LABEL, H_NH, H_SEARCHED, H_RBAR, H_SIGR, H_VFX, H_VFY, H_VFZ, H_SIGMA, H_LX2, 
 # every symbol include/vr.h declares
 EXPORTS = ("vr_params_default", "vr_create", "vr_destroy", "vr_last_error", "vr_workspace_size",
            "vr_sync", "vr_fof3d", "vr_velden", "vr_outlier_ratio", "vr_fof6d",
-           "vr_fof6d_field", "vr_clean_groups", "vr_find_substructure")
+           "vr_fof6d_field", "vr_clean_groups", "vr_grow_params_default", "vr_grow_groups",
+           "vr_find_substructure")
 
 
 class VrError(RuntimeError):
@@ -53,6 +54,23 @@ class Params(ctypes.Structure):
         for k, v in kw.items():
             setattr(p, k, v)
         return p
+
+
+class GrowParams(ctypes.Structure):
+    """Mirror of vr_grow_params (include/vr.h): gamma factors of the relaxed pass and
+    the merge fraction."""
+
+    _fields_ = [("gamma_ell", ctypes.c_double), ("gamma_x", ctypes.c_double),
+                ("gamma_vr", ctypes.c_double), ("gamma_theta", ctypes.c_double),
+                ("f_merge", ctypes.c_double)]
+
+    @classmethod
+    def default(cls, **kw) -> "GrowParams":
+        g = cls()
+        lib().vr_grow_params_default(ctypes.byref(g))
+        for k, v in kw.items():
+            setattr(g, k, v)
+        return g
 
 
 _lock = threading.Lock()
@@ -92,6 +110,9 @@ def lib(build_if_missing: bool = True):
                                                   ctypes.POINTER(i64), vp, sz, vp]),
                 "vr_clean_groups": (ctypes.c_int, [vp, vp, i64, P, dbl, vp, ctypes.POINTER(i64),
                                                    vp, sz, vp]),
+                "vr_grow_params_default": (None, [ctypes.POINTER(GrowParams)]),
+                "vr_grow_groups": (ctypes.c_int, [vp, vp, vp, vp, i64, vp, vp, i64, P,
+                                                  ctypes.POINTER(GrowParams), vp, vp, sz, vp]),
                 "vr_find_substructure": (ctypes.c_int, [vp, vp, vp, i64, vp, dbl, dbl, P,
                                                         ctypes.c_int, vp, vp, vp, vp, vp,
                                                         ctypes.POINTER(i64), vp, sz, vp]),
@@ -223,6 +244,20 @@ class Context:
                                         _ptr(halos), ctypes.byref(nh), _ptr(ws), ws.numel(),
                                         _stream(stream)))
         return label6, halos[: nh.value]
+
+    def grow_groups(self, pos, vel, ell, label, halo_params, label6,
+                    params: Params | None = None, grow: GrowParams | None = None, stream=None):
+        """Two-stage linking (vr_grow_groups): grows the groups of label6 in place."""
+        n = pos.shape[0]
+        params = params or Params.default()
+        grow = grow or GrowParams.default()
+        halo_params = halo_params.contiguous()
+        ws = self.workspace(n, params)
+        self.check(lib().vr_grow_groups(self.h, _ptr(pos), _ptr(vel), _ptr(ell), n, _ptr(label),
+                                        _ptr(halo_params), halo_params.shape[0],
+                                        ctypes.byref(params), ctypes.byref(grow), _ptr(label6),
+                                        _ptr(ws), ws.numel(), _stream(stream)))
+        return label6
 
     def clean_groups(self, ell, label6, params: Params | None = None, beta: float = 1.0,
                      stream=None):
