@@ -14,9 +14,9 @@ the slowest rank's time. Rank 0 prints one JSON line.
 
 The headline runs the batched form (each stage one launch over all halos); the same
 inputs are then timed in the plain form (each stage launched once per halo) and reported
-under "plain_form". Field 6DFOF of the 3DFOF halos and the significance cleaning of the
-step's outlier groups are timed afterwards on the same box and reported under
-"next_rows" (outside the headline).
+under "plain_form". Field 6DFOF of the 3DFOF halos, the significance cleaning of the
+step's outlier groups and their two-stage growth are timed afterwards on the same box and
+reported under "next_rows" (outside the headline).
 
 --impl reference times the FP64 C oracle (the path's reference implementation) on the
 host cores, one step = the oracle pipeline over a bounded sample of the workload (a 64^3
@@ -272,8 +272,9 @@ def run_ours(args):
                "d2h_bytes_per_step": int(hl3.numel() * 4 + hl6.numel() * 4)}
 
     # ---- rows beyond the headline step, on the same box (timed separately, 3 calls each):
-    #      field 6DFOF of the 3DFOF halos (Sec. 2.1) and significance cleaning of the
-    #      outlier groups the step produced (Sec. 2.2, Eq. ellsig)
+    #      field 6DFOF of the 3DFOF halos (Sec. 2.1), significance cleaning of the outlier
+    #      groups the step produced (Sec. 2.2, Eq. ellsig) and their two-stage growth with
+    #      the merge threshold (Sec. 2.2)
     next_rows = None
     if args.next_rows:
         lx = 0.2 * synth.mean_spacing(box.n)
@@ -288,11 +289,22 @@ def run_ours(args):
             l6c.copy_(out["label6"])
             return ctx.clean_groups(out["ell"], l6c, P, 1.0)
 
+        from paper_1902_01010_gb300 import GrowParams
+
+        l6g = out["label6"].clone()
+        hs_g = out["halos"][: out["nhalo"]].contiguous()
+        gp = GrowParams.default()
+
+        def grow():
+            l6g.copy_(out["label6"])
+            ctx.grow_groups(pos, vel, out["ell"], lab, hs_g, l6g, P, gp)
+
         field()
         clean()
+        grow()
         ctx.sync()
         res = {}
-        for name, f in (("field_6dfof", field), ("clean_groups", clean)):
+        for name, f in (("field_6dfof", field), ("clean_groups", clean), ("two_stage_linking", grow)):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize(dev)
             e0.record(stream)
@@ -311,6 +323,14 @@ def run_ours(args):
                                     "groups_in": int(len(np.unique(
                                         out["label6"].cpu().numpy()[out["label6"].cpu().numpy() >= 0]))),
                                     "beta": 1.0})
+        a6 = out["label6"].cpu().numpy()
+        ag = l6g.cpu().numpy()
+        res["two_stage_linking"].update({
+            "particles_in_groups_before": int((a6 >= 0).sum()),
+            "particles_in_groups_after": int((ag >= 0).sum()),
+            "groups_before": int(len(np.unique(a6[a6 >= 0]))),
+            "groups_after": int(len(np.unique(ag[ag >= 0]))),
+            "gamma": [gp.gamma_ell, gp.gamma_x, gp.gamma_vr, gp.gamma_theta], "f_merge": gp.f_merge})
         next_rows = res
 
     # ---- the other launch form on the same inputs: one launch per halo and stage
