@@ -90,6 +90,8 @@ def _lib_():
             "or_clean_groups": (i64, [vp, vp, i64, dbl, dbl, i32]),
             "or_grow_halo": (ctypes.c_int, [vp, vp, vp, i64, vp, vp, vp, dbl, dbl, dbl,
                                             ctypes.c_int, ctypes.c_int, vp, dbl, vp]),
+            "or_core_search": (i64, [vp, vp, vp, i64, vp, dbl, dbl, dbl, dbl, ctypes.c_int,
+                                     dbl, dbl, i32, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -288,6 +290,45 @@ def two_stage(pos, vel, label3, ell, label6, halo_rows, nmin=20, **kw) -> np.nda
         out[m] = grow_halo(unwrap(pos, m), vel, m, np.asarray(ell, np.float64)[m],
                            np.asarray(label6, np.int32)[m], prm, **kw)
     return out
+
+
+CORE_DEFAULTS = dict(ax=0.8, av=1.0, n_loop=5, f_c=0.02, an=1.2)  # Table 1, core search
+
+
+def core_search_halo(upos, vel, members, lab6, lx, lv, ax=0.8, av=1.0, n_loop=5, f_c=0.02,
+                     an=1.2, nmin=20):
+    """Core search inside one halo (Sec. 2.3, Eq. coreloop). lab6 per member (None: no
+    substructure). Returns (core label per member, level per member, number of cores)."""
+    upos = _c(upos, np.int64)
+    vel = _c(vel, np.float32)
+    members = _c(members, np.int32)
+    nh = members.shape[0]
+    l6 = None if lab6 is None else _c(lab6, np.int32)
+    core = np.empty(nh, np.int32)
+    lev = np.empty(nh, np.int32)
+    nc = _lib_().or_core_search(_p(upos), _p(vel), _p(members), nh, _p(l6), float(lx), float(lv),
+                                ax, av, n_loop, f_c, an, nmin, _p(core), _p(lev))
+    return core, lev, int(nc)
+
+
+def core_search(pos, vel, label3, label6, lx, alpha_v=1.25, nsearch_min=160, nmin=20, **kw):
+    """core_search_halo over every halo with N_H >= nsearch_min, lv = alpha_v sigma_v
+    (halo_frame). Returns (core, level) per particle."""
+    n = len(pos)
+    core = np.full(n, -1, np.int32)
+    lev = np.full(n, -1, np.int32)
+    off, mem = halos(label3, nmin)
+    for h in range(len(off) - 1):
+        m = mem[off[h]:off[h + 1]]
+        if len(m) < nsearch_min:
+            continue
+        lv = alpha_v * halo_frame(vel, m)[3]
+        c, l, _ = core_search_halo(unwrap(pos, m), vel, m,
+                                   None if label6 is None else np.asarray(label6, np.int32)[m],
+                                   lx, lv, nmin=nmin, **kw)
+        core[m] = c
+        lev[m] = l
+    return core, lev
 
 
 def ell_bar(ell_th: float) -> float:

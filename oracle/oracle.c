@@ -1171,6 +1171,72 @@ int or_grow_halo(const int64_t *upos, const float *vel, const int32_t *members, 
   return 0;
 }
 
+/* --------------------------------------------------------- core search (Sec. 2.3) */
+
+/* Core search inside one halo (Sec. 2.3, "Core Identification", Eq. coreloop). The
+ * "background" starts as the members outside substructure (lab6 < 0). Loop l = 0, 1,
+ * ..., n_loop - 1: a 6DFOF (Eq. fof6d, all background members candidates) with
+ * lx_l = alpha_x,C^l lx and lv_l = alpha_v,C^l lv, each length obtained by repeated
+ * multiplication from lx and lv; groups count if they hold >= nmin and >= N_min,C =
+ * f_C N_H alpha_N,C^l members (also by repeated multiplication, compared as reals).
+ * With no such group the loop stops. Otherwise the largest group (ties: the smaller
+ * label) becomes the next background, the "primary core", and every other group is a
+ * candidate core of level l. After the loop the last primary core is labelled too.
+ * Labels are the minimum particle index of each core.
+ *   out_core [nh]: core label of each member, -1 if none; out_level [nh]: its level.
+ * Returns the number of cores (candidate cores + the primary core). */
+int64_t or_core_search(const int64_t *upos, const float *vel, const int32_t *members,
+                       int64_t nh, const int32_t *lab6, double lx, double lv, double ax,
+                       double av, int n_loop, double f_c, double an, int32_t nmin,
+                       int32_t *out_core, int32_t *out_level) {
+  for (int64_t i = 0; i < nh; ++i) { out_core[i] = -1; out_level[i] = -1; }
+  if (nh <= 0) return 0;
+  uint8_t *bg = (uint8_t *)malloc((size_t)nh);
+  int32_t *l6 = (int32_t *)malloc((size_t)nh * sizeof(int32_t));
+  int64_t *size = (int64_t *)calloc((size_t)nh, sizeof(int64_t));
+  for (int64_t i = 0; i < nh; ++i) bg[i] = lab6 ? lab6[i] < 0 : 1;
+  double lxl = lx, lvl = lv, thr = f_c * (double)nh;
+  int64_t ncore = 0, prim = -1;
+  int prim_level = -1;
+  for (int l = 0; l < n_loop; ++l) {
+    if (l > 0) { lxl = lxl * ax; lvl = lvl * av; thr = thr * an; }
+    double prm[5] = {lxl * lxl, lvl * lvl, 0.0, 0.0, 0.0};
+    or_fof6d_halo(upos, vel, members, nh, bg, prm, 0.0, 0.0, 1, 0, 1, l6);
+    /* group sizes by label slot (labels are member indices: the slot of a label) */
+    for (int64_t i = 0; i < nh; ++i) size[i] = 0;
+    for (int64_t i = 0; i < nh; ++i)
+      if (l6[i] >= 0) size[or_slot(members, nh, l6[i])]++;
+    int64_t big = -1;
+    for (int64_t i = 0; i < nh; ++i) {
+      if (size[i] < nmin || (double)size[i] < thr) continue;
+      if (big < 0 || size[i] > size[big]) big = i; /* ascending slots: ties keep the smaller */
+    }
+    if (big < 0) break;
+    for (int64_t i = 0; i < nh; ++i) {
+      if (l6[i] < 0) { bg[i] = 0; continue; }
+      const int64_t g = or_slot(members, nh, l6[i]);
+      if (size[g] < nmin || (double)size[g] < thr) { bg[i] = 0; continue; }
+      if (g == big) continue; /* stays in the background */
+      bg[i] = 0;
+      out_core[i] = l6[i];
+      out_level[i] = l;
+    }
+    for (int64_t i = 0; i < nh; ++i)
+      if (i != big && size[i] >= nmin && (double)size[i] >= thr) ncore++;
+    prim = big;
+    prim_level = l;
+  }
+  if (prim >= 0) {
+    for (int64_t i = 0; i < nh; ++i)
+      if (bg[i]) { out_core[i] = members[prim]; out_level[i] = prim_level; }
+    ncore++;
+  }
+  free(size);
+  free(l6);
+  free(bg);
+  return ncore;
+}
+
 /* ------------------------------------------------------- field 6DFOF (Sec. 2.1) */
 
 /* Field halos (Sec. 2.1, Eq. fof6d): every 3DFOF group of >= nmin members is split by a
