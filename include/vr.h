@@ -236,6 +236,42 @@ vr_status vr_grow_groups(vr_ctx *ctx, const int32_t *pos, const float *vel, cons
                          int64_t nhalo, const vr_params *p, const vr_grow_params *gp,
                          int32_t *label6, void *ws, size_t ws_bytes, void *stream);
 
+/* Core search (Sec. 2.3, "Core Identification", Eq. coreloop) inside every halo of >=
+ * p->nsearch_min members. The background starts as the members outside substructure
+ * (label6 < 0; every member when label6 is NULL). Loop l = 0 .. n_loop - 1: a 6DFOF
+ * (Eq. fof6d, predicate and rounding as in vr_fof6d, V_r / Theta_op off) over the
+ * background with lx_l = alpha_x^l lx and lv_l = alpha_v,C^l lv, lv = alpha_v
+ * sigma_v (sigma_v = |Sigma|^(1/6) of the halo), each by repeated multiplication;
+ * groups count with >= p->nmin and >= f_c N_H alpha_n^l members (also by repeated
+ * multiplication, compared as reals). Without such a group the halo's search stops.
+ * Otherwise its largest group (ties: smaller label) is the next background, the
+ * "primary core", and every other group is a candidate core of level l. The last
+ * primary core is labelled at the end. Table 1 defaults (vr_core_params_default):
+ * alpha_x,C 0.8, alpha_v,C 1.0, n_loop,C 5, f_C 0.02, alpha_N,C 1.2. */
+typedef struct {
+  double alpha_x, alpha_v;  /* length factors per loop (alpha_x,C, alpha_v,C) */
+  int32_t n_loop;           /* loops n_loop,C */
+  double f_c, alpha_n;      /* N_min,C = f_c N_H alpha_n^l */
+} vr_core_params;
+
+void vr_core_params_default(vr_core_params *c);
+
+/*   label6      int32 [n] substructure labels (may be NULL)
+ *   lx, alpha_v the halo linking length (lattice units) and the velocity factor of the
+ *               field 6DFOF (Table 1: 0.2 mean spacing, 1.25)
+ *   core, level int32 [n] out: minimum particle index of the member's core and the loop
+ *               at which it was found; -1 for particles in no core
+ *   ncores      int64 host pointer out (may be NULL): candidate cores + primary cores
+ *   halo_stats  double [n/nmin + 1][VR_HALO_COLS] out: frame rows; LX2, LV2 and
+ *               SEARCHED hold the last loop's values
+ *   nhalo       int64 host pointer out (may be NULL)
+ * This call synchronises `stream`. */
+vr_status vr_core_search(vr_ctx *ctx, const int32_t *pos, const float *vel, int64_t n,
+                         const int32_t *label, const int32_t *label6, double lx, double alpha_v,
+                         const vr_params *p, const vr_core_params *cp, int32_t *core,
+                         int32_t *level, int64_t *ncores, double *halo_stats, int64_t *nhalo,
+                         void *ws, size_t ws_bytes, void *stream);
+
 /* Cleaning of outlier groups (Sec. 2.2, "Cleaning the catalogue", Eq. ellsig). A group
  * of N particles (equal labels >= 0 in label6) is significant iff
  *   <ell> >= ell_bar(p->ell_th) (1 + beta/sqrt(N)),
@@ -284,7 +320,7 @@ vr_status vr_fof3d_noalloc(const int32_t *pos, int64_t n, int64_t link_d2, int32
  * (no counterpart in the paper: instrumentation of this library)
  * Per-kernel device timing with CUDA events recorded on the launching stream; off by
  * default. Kernel names: "fof_link", "velden_big", "velden_small", "halo_frame",
- * "cells_build", "cells_build_big", "ratio", "ell_fit", "link6", "clean". */
+ * "cells_build", "cells_build_big", "ratio", "ell_fit", "link6", "clean", "core_link". */
 
 /* Enables (1) or disables (0) event timing of the named kernels for this context. */
 vr_status vr_timing_enable(vr_ctx *ctx, int enable);

@@ -30,7 +30,8 @@ namespace {
 __global__ void k_cand_flags(const uint32_t *__restrict__ hid, int64_t nhp,
                              const float4 *__restrict__ v, const float *__restrict__ ell,
                              const double *__restrict__ hp, int64_t nhalo, double ell_th,
-                             const int32_t *__restrict__ tag, uint32_t *__restrict__ flag) {
+                             const int32_t *__restrict__ tag, const uint8_t *__restrict__ mask,
+                             uint32_t *__restrict__ flag) {
   int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (m > nhp) return;
   if (m == nhp) {
@@ -43,6 +44,7 @@ __global__ void k_cand_flags(const uint32_t *__restrict__ hid, int64_t nhp,
     const int pi = __float_as_int(v[m].w);
     c = (double)ell[pi] >= ell_th || (tag && tag[pi] >= 0);  // false for NaN
   }
+  if (c && mask) c = mask[__float_as_int(v[m].w)] != 0;
   flag[m] = c ? 1u : 0u;
 }
 
@@ -401,6 +403,7 @@ struct Cands {
   uint32_t nc = 0, ntiles = 0;
   int4 *cu;
   float4 *cv;
+  uint32_t *chid;  // halo of each candidate
   uint32_t *coff, *toff, *thalo;
   int4 *tmin, *tmax;
   int *parent, *minidx, *size;
@@ -408,14 +411,14 @@ struct Cands {
 
 vr_status prep_cands(vr_ctx *ctx, const HaloSeg &g, int nmin, Arena &ar, const float *ell,
                      double ell_thr, const int32_t *tag, const double *hp, int64_t nhalo,
-                     cudaStream_t s, Cands *C) {
+                     cudaStream_t s, Cands *C, const uint8_t *mask = nullptr) {
   const int64_t H = g.H, nhp = g.NHP;
   int64_t hmax = g.n / (nmin > 0 ? nmin : 1) + 2;
   int64_t tmaxn = g.n / 32 + hmax + 2;
   uint32_t *flag = ar.take<uint32_t>(g.n + 1);
   C->cu = ar.take<int4>(g.n);
   C->cv = ar.take<float4>(g.n);
-  uint32_t *chid = ar.take<uint32_t>(g.n);
+  uint32_t *chid = C->chid = ar.take<uint32_t>(g.n);
   C->coff = ar.take<uint32_t>(hmax + 1);
   C->toff = ar.take<uint32_t>(hmax + 1);
   C->thalo = ar.take<uint32_t>(tmaxn);
@@ -427,7 +430,8 @@ vr_status prep_cands(vr_ctx *ctx, const HaloSeg &g, int nmin, Arena &ar, const f
   void *scr = ar.take<char>(scan_scratch_bytes<uint32_t>(g.n + 1));
   if (!ar.ok()) return set_error(ctx, VR_ERR_WORKSPACE_TOO_SMALL, "workspace too small");
   const int T = 256;
-  k_cand_flags<<<grid_for(nhp + 1, T), T, 0, s>>>(g.hid, nhp, g.v, ell, hp, nhalo, ell_thr, tag, flag);
+  k_cand_flags<<<grid_for(nhp + 1, T), T, 0, s>>>(g.hid, nhp, g.v, ell, hp, nhalo, ell_thr, tag,
+                                                  mask, flag);
   VR_LAUNCHED(ctx, "k_cand_flags");
   VR_CUDA(ctx, exclusive_scan<uint32_t>(flag, flag, nhp + 1, scr, s));
   k_cand_compact<<<grid_for(nhp, T), T, 0, s>>>(flag, g.hid, nhp, g.u, g.v, C->cu, C->cv, chid);
@@ -528,6 +532,116 @@ __global__ void k_grow_out(int *gpar, const int *__restrict__ grown, const float
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nc || grown[c] < 0) return;
   label6[__float_as_int(cv[c].w)] = minidx[uf_find(gpar, grown[c])];
+}
+
+// ------------------------------------------------------------- core search kernels
+
+// Initial background: members of halos of >= nsearch_min members outside substructure.
+__global__ void k_core_init(const uint32_t *__restrict__ hoff, const uint32_t *__restrict__ hid,
+                            const float4 *__restrict__ v, int64_t nhp, int nsearch_min,
+                            const int32_t *__restrict__ label6, uint8_t *__restrict__ mask) {
+  const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= nhp) return;
+  const uint32_t h = hid[m];
+  const int pi = __float_as_int(v[m].w);
+  mask[pi] = (hoff[h + 1] - hoff[h] >= (uint32_t)nsearch_min && (!label6 || label6[pi] < 0)) ? 1 : 0;
+}
+
+// Loop l: lengths and thresholds of every halo still searching (Eq. coreloop, by repeated
+// multiplication), written into the rows the linker reads.
+__global__ void k_core_rows(int64_t H, const uint32_t *__restrict__ hoff, int l, double lx2,
+                            double alpha_v, double av, double f_c, double an, int nsearch_min,
+                            int *__restrict__ active, double *__restrict__ lv,
+                            double *__restrict__ thr, unsigned long long *__restrict__ best,
+                            double *__restrict__ hs) {
+  const int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= H) return;
+  double *row = hs + h * VR_HALO_COLS;
+  if (l == 0) {
+    active[h] = hoff[h + 1] - hoff[h] >= (uint32_t)nsearch_min;
+    lv[h] = alpha_v * row[VR_H_SIGMA];
+    thr[h] = f_c * (double)(hoff[h + 1] - hoff[h]);
+  } else {
+    lv[h] = lv[h] * av;
+    thr[h] = thr[h] * an;
+  }
+  best[h] = 0;
+  row[VR_H_SEARCHED] = active[h] ? 1.0 : 0.0;
+  row[VR_H_LX2] = lx2;
+  row[VR_H_LV2] = lv[h] * lv[h];
+}
+
+__device__ __forceinline__ bool core_ok(int size, int nmin, double thr) {
+  return size >= nmin && (double)size >= thr;
+}
+
+// The largest qualifying group of each halo: max of (size << 32 | ~label).
+__global__ void k_core_best(int *parent, const uint32_t *__restrict__ chid, int64_t nc,
+                            const int *__restrict__ minidx, const int *__restrict__ size, int nmin,
+                            const double *__restrict__ thr, unsigned long long *__restrict__ best) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc || uf_find(parent, (int)c) != (int)c) return;
+  const uint32_t h = chid[c];
+  if (!core_ok(size[c], nmin, thr[h])) return;
+  atomicMax(&best[h], ((unsigned long long)(uint32_t)size[c] << 32) |
+                          (unsigned long long)(~(uint32_t)minidx[c]));
+}
+
+// Members of the largest group stay in the background; members of other qualifying
+// groups become cores of level l; the rest leave the background. Halos without a
+// qualifying group keep their background (their last primary core).
+__global__ void k_core_mark(int *parent, const uint32_t *__restrict__ chid,
+                            const float4 *__restrict__ cv, int64_t nc,
+                            const int *__restrict__ minidx, const int *__restrict__ size, int nmin,
+                            const double *__restrict__ thr,
+                            const unsigned long long *__restrict__ best, int l,
+                            uint8_t *__restrict__ mask, int32_t *__restrict__ core,
+                            int32_t *__restrict__ level, unsigned long long *__restrict__ ncores) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  const uint32_t h = chid[c];
+  const unsigned long long b = best[h];
+  if (!b) return;
+  const int r = uf_find(parent, (int)c);
+  const int pi = __float_as_int(cv[c].w);
+  if (!core_ok(size[r], nmin, thr[h])) {
+    mask[pi] = 0;
+    return;
+  }
+  const int lab = minidx[r];
+  if ((uint32_t)lab == ~(uint32_t)b) return;  // the primary core
+  mask[pi] = 0;
+  core[pi] = lab;
+  level[pi] = l;
+  if (r == (int)c) atomicAdd(ncores, 1ull);
+}
+
+__global__ void k_core_halos(int64_t H, const unsigned long long *__restrict__ best, int l,
+                             int *__restrict__ active, int *__restrict__ last,
+                             int *__restrict__ prim) {
+  const int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= H || !active[h]) return;
+  if (!best[h]) {
+    active[h] = 0;
+    return;
+  }
+  last[h] = l;
+  prim[h] = (int)(~(uint32_t)best[h]);
+}
+
+// The last primary core of every halo that found one.
+__global__ void k_core_final(const uint32_t *__restrict__ hid, const float4 *__restrict__ v,
+                             int64_t nhp, const uint8_t *__restrict__ mask,
+                             const int *__restrict__ last, const int *__restrict__ prim,
+                             int32_t *__restrict__ core, int32_t *__restrict__ level) {
+  const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= nhp) return;
+  const uint32_t h = hid[m];
+  const int pi = __float_as_int(v[m].w);
+  if (mask[pi] && last[h] >= 0) {
+    core[pi] = prim[h];
+    level[pi] = last[h];
+  }
 }
 
 }  // namespace
@@ -651,6 +765,84 @@ size_t grow_bytes(int64_t n, int nmin) {
   ar.take<u64>(grow_table_cap(n));
   ar.take<uint32_t>(grow_table_cap(n));
   return ar.off;
+}
+
+vr_status run_cores(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, const vr_core_params *cp,
+                    double lx, double alpha_v, Arena &ar, const int32_t *label6, double *hs,
+                    int32_t *core, int32_t *level, int64_t *ncores, cudaStream_t s) {
+  if (ncores) *ncores = 0;
+  const int64_t H = g.H, n = g.n;
+  uint8_t *mask = ar.take<uint8_t>(n);
+  int *active = ar.take<int>(H + 1);
+  int *last = ar.take<int>(H + 1);
+  int *prim = ar.take<int>(H + 1);
+  double *lv = ar.take<double>(H + 1);
+  double *thr = ar.take<double>(H + 1);
+  unsigned long long *best = ar.take<unsigned long long>(H + 1);
+  unsigned long long *cnt = ar.take<unsigned long long>(1);
+  if (!ar.ok()) return set_error(ctx, VR_ERR_WORKSPACE_TOO_SMALL, "workspace too small");
+  const int T = 256;
+  vr_status st0 = fill_i32(ctx, core, n, -1, s);
+  if (st0 == VR_OK) st0 = fill_i32(ctx, level, n, -1, s);
+  if (st0 != VR_OK || H == 0) return st0;
+  VR_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
+  k_fill_i32<<<grid_for(H, T), T, 0, s>>>(last, H, -1);
+  VR_LAUNCHED(ctx, "k_fill_i32");
+  k_core_init<<<grid_for(g.NHP, T), T, 0, s>>>(g.hoff, g.hid, g.v, g.NHP, p->nsearch_min, label6, mask);
+  VR_LAUNCHED(ctx, "k_core_init");
+  const size_t mark = ar.off;
+  double lxl = lx;
+  for (int l = 0; l < cp->n_loop; ++l) {
+    if (l > 0) lxl = lxl * cp->alpha_x;
+    k_core_rows<<<grid_for(H, T), T, 0, s>>>(H, g.hoff, l, lxl * lxl, alpha_v, cp->alpha_v,
+                                              cp->f_c, cp->alpha_n, p->nsearch_min, active, lv,
+                                              thr, best, hs);
+    VR_LAUNCHED(ctx, "k_core_rows");
+    ar.off = mark;
+    Cands C;
+    vr_status st = prep_cands(ctx, g, p->nmin, ar, nullptr, 0.0, nullptr, hs, H, s, &C, mask);
+    if (st != VR_OK) return st;
+    if (C.nc == 0) break;
+    GrowArgs G{};
+    VR_TIMED(ctx, "core_link", s, k_link6<kLink><<<grid_for(C.ntiles, 4), 128, 0, s>>>(
+        C.toff, C.coff, C.thalo, 0, C.ntiles, C.cu, C.cv, C.tmin, C.tmax, hs, 0.0, 0.0, 1, 0,
+        C.parent, G));
+    VR_LAUNCHED(ctx, "k_link6");
+    k_cand_roots<<<grid_for(C.nc, T), T, 0, s>>>(C.parent, C.cv, C.nc, C.minidx, C.size);
+    VR_LAUNCHED(ctx, "k_cand_roots");
+    k_core_best<<<grid_for(C.nc, T), T, 0, s>>>(C.parent, C.chid, C.nc, C.minidx, C.size, p->nmin,
+                                                 thr, best);
+    VR_LAUNCHED(ctx, "k_core_best");
+    k_core_mark<<<grid_for(C.nc, T), T, 0, s>>>(C.parent, C.chid, C.cv, C.nc, C.minidx, C.size,
+                                                 p->nmin, thr, best, l, mask, core, level, cnt);
+    VR_LAUNCHED(ctx, "k_core_mark");
+    k_core_halos<<<grid_for(H, T), T, 0, s>>>(H, best, l, active, last, prim);
+    VR_LAUNCHED(ctx, "k_core_halos");
+  }
+  k_core_final<<<grid_for(g.NHP, T), T, 0, s>>>(g.hid, g.v, g.NHP, mask, last, prim, core, level);
+  VR_LAUNCHED(ctx, "k_core_final");
+  // cores = candidate cores + one primary core per halo that found a group
+  VR_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned + 40, cnt, sizeof(unsigned long long),
+                               cudaMemcpyDeviceToHost, s));
+  std::vector<int> lh(H);
+  VR_CUDA(ctx, cudaMemcpyAsync(lh.data(), last, H * sizeof(int), cudaMemcpyDeviceToHost, s));
+  VR_CUDA(ctx, cudaStreamSynchronize(s));
+  int64_t np = 0;
+  for (int64_t h = 0; h < H; ++h) np += lh[h] >= 0;
+  if (ncores) *ncores = (int64_t)ctx->h_pinned[40] + np;
+  return VR_OK;
+}
+
+size_t cores_bytes(int64_t n, int nmin) {
+  Arena ar;
+  const int64_t hmax = n / (nmin > 0 ? nmin : 1) + 2;
+  ar.take<uint8_t>(n);
+  for (int k = 0; k < 3; ++k) ar.take<int>(hmax + 1);
+  ar.take<double>(hmax + 1);
+  ar.take<double>(hmax + 1);
+  ar.take<unsigned long long>(hmax + 1);
+  ar.take<unsigned long long>(1);
+  return ar.off + fof6d_bytes(n, nmin) + 4096;
 }
 
 }  // namespace vr

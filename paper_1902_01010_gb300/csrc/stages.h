@@ -28,6 +28,11 @@ size_t grow_bytes(int64_t n, int nmin);
 vr_status run_grow(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, const vr_grow_params *gp,
                    Arena &ar, const float *ell, const double *hp, int64_t nhalo, int32_t *label6,
                    cudaStream_t s);
+size_t cores_bytes(int64_t n, int nmin);
+// Core search (Eq. coreloop) on a segmentation whose halo rows hold SIGMA.
+vr_status run_cores(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, const vr_core_params *cp,
+                    double lx, double alpha_v, Arena &ar, const int32_t *label6, double *hs,
+                    int32_t *core, int32_t *level, int64_t *ncores, cudaStream_t s);
 size_t clean_bytes(int64_t n);
 // Significance cleaning of groups (Eq. ellsig); synchronises the stream.
 vr_status run_clean(vr_ctx *ctx, const float *ell, int64_t n, const vr_params *p, double beta,

@@ -14,9 +14,10 @@ size_t ws_substructure(int64_t n, const vr_params *p) {
   size_t a = velden_bytes(n, p->nmin), b = background_bytes(n, p), c = fof6d_bytes(n, p->nmin);
   size_t m = a > b ? a : b;
   m = m > c ? m : c;
-  const size_t cl = clean_bytes(n), gr = grow_bytes(n, p->nmin);
+  const size_t cl = clean_bytes(n), gr = grow_bytes(n, p->nmin), co = cores_bytes(n, p->nmin);
   m = m > cl ? m : cl;
   m = m > gr ? m : gr;
+  m = m > co ? m : co;
   return halo_seg_bytes(n, p->nmin) + m + 4096;
 }
 
@@ -169,6 +170,43 @@ vr_status vr_grow_groups(vr_ctx *ctx, const int32_t *pos, const float *vel, cons
     return set_error(ctx, VR_ERR_INVALID_ARG, "nhalo = %lld but the labels define %lld halos",
                      (long long)nhalo, (long long)g.H);
   if ((st = run_grow(ctx, g, p, gp, ar, ell, halo_params, nhalo, label6, s)) != VR_OK) return st;
+  return read_status(ctx, s, nullptr);
+}
+
+void vr_core_params_default(vr_core_params *c) {
+  if (!c) return;
+  c->alpha_x = 0.8;
+  c->alpha_v = 1.0;
+  c->n_loop = 5;
+  c->f_c = 0.02;
+  c->alpha_n = 1.2;
+}
+
+vr_status vr_core_search(vr_ctx *ctx, const int32_t *pos, const float *vel, int64_t n,
+                         const int32_t *label, const int32_t *label6, double lx, double alpha_v,
+                         const vr_params *p, const vr_core_params *cp, int32_t *core,
+                         int32_t *level, int64_t *ncores, double *halo_stats, int64_t *nhalo,
+                         void *ws, size_t ws_bytes, void *stream) {
+  if (!ctx) return VR_ERR_INVALID_ARG;
+  vr_status st = common_checks(ctx, n, p);
+  if (st != VR_OK) return st;
+  if (ncores) *ncores = 0;
+  if (nhalo) *nhalo = 0;
+  if (n == 0) return VR_OK;
+  if (!pos || !vel || !label || !cp || !core || !level || !halo_stats || !ws)
+    return set_error(ctx, VR_ERR_INVALID_ARG, "NULL pointer");
+  if (!(lx > 0.0) || !(alpha_v > 0.0) || !(cp->alpha_x > 0.0) || !(cp->alpha_v > 0.0) ||
+      cp->n_loop < 0 || cp->n_loop > 1000 || !(cp->f_c >= 0.0) || !(cp->alpha_n > 0.0))
+    return set_error(ctx, VR_ERR_INVALID_ARG, "bad core search parameters");
+  cudaStream_t s = (cudaStream_t)stream;
+  Arena ar(ws, ws_bytes);
+  HaloSeg g;
+  if ((st = build_halos(ctx, pos, vel, n, label, p->nmin, p->nse, ar, s, &g)) != VR_OK) return st;
+  if ((st = run_halo_frame(ctx, g, p->nsearch_min, halo_stats, s)) != VR_OK) return st;
+  if ((st = run_cores(ctx, g, p, cp, lx, alpha_v, ar, label6, halo_stats, core, level, ncores,
+                      s)) != VR_OK)
+    return st;
+  if (nhalo) *nhalo = g.H;
   return read_status(ctx, s, nullptr);
 }
 

@@ -26,7 +26,7 @@ H_LABEL, H_NH, H_SEARCHED, H_RBAR, H_SIGR, H_VFX, H_VFY, H_VFZ, H_SIGMA, H_LX2, 
 EXPORTS = ("vr_params_default", "vr_create", "vr_destroy", "vr_last_error", "vr_workspace_size",
            "vr_sync", "vr_fof3d", "vr_velden", "vr_outlier_ratio", "vr_fof6d",
            "vr_fof6d_field", "vr_clean_groups", "vr_grow_params_default", "vr_grow_groups",
-           "vr_find_substructure")
+           "vr_core_params_default", "vr_core_search", "vr_find_substructure")
 
 
 class VrError(RuntimeError):
@@ -73,6 +73,21 @@ class GrowParams(ctypes.Structure):
         return g
 
 
+class CoreParams(ctypes.Structure):
+    """Mirror of vr_core_params (include/vr.h)."""
+
+    _fields_ = [("alpha_x", ctypes.c_double), ("alpha_v", ctypes.c_double),
+                ("n_loop", ctypes.c_int32), ("f_c", ctypes.c_double), ("alpha_n", ctypes.c_double)]
+
+    @classmethod
+    def default(cls, **kw) -> "CoreParams":
+        c = cls()
+        lib().vr_core_params_default(ctypes.byref(c))
+        for k, v in kw.items():
+            setattr(c, k, v)
+        return c
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -111,6 +126,11 @@ def lib(build_if_missing: bool = True):
                 "vr_clean_groups": (ctypes.c_int, [vp, vp, i64, P, dbl, vp, ctypes.POINTER(i64),
                                                    vp, sz, vp]),
                 "vr_grow_params_default": (None, [ctypes.POINTER(GrowParams)]),
+                "vr_core_params_default": (None, [ctypes.POINTER(CoreParams)]),
+                "vr_core_search": (ctypes.c_int, [vp, vp, vp, i64, vp, vp, dbl, dbl, P,
+                                                  ctypes.POINTER(CoreParams), vp, vp,
+                                                  ctypes.POINTER(i64), vp, ctypes.POINTER(i64),
+                                                  vp, sz, vp]),
                 "vr_grow_groups": (ctypes.c_int, [vp, vp, vp, vp, i64, vp, vp, i64, P,
                                                   ctypes.POINTER(GrowParams), vp, vp, sz, vp]),
                 "vr_find_substructure": (ctypes.c_int, [vp, vp, vp, i64, vp, dbl, dbl, P,
@@ -258,6 +278,31 @@ class Context:
                                         ctypes.byref(params), ctypes.byref(grow), _ptr(label6),
                                         _ptr(ws), ws.numel(), _stream(stream)))
         return label6
+
+    def core_search(self, pos, vel, label, label6, lx: float, alpha_v: float = 1.25,
+                    params: Params | None = None, cores: CoreParams | None = None, out=None,
+                    stream=None):
+        """Core search (vr_core_search). label6 may be None. Returns a dict with core,
+        level, ncores, halos (rows) and nhalo."""
+        n = pos.shape[0]
+        params = params or Params.default()
+        cores = cores or CoreParams.default()
+        if out is None:
+            dev = pos.device
+            out = dict(core=torch.empty(n, dtype=torch.int32, device=dev),
+                       level=torch.empty(n, dtype=torch.int32, device=dev),
+                       halos=torch.empty((n // max(params.nmin, 1) + 1, HALO_COLS),
+                                         dtype=torch.float64, device=dev))
+        nc, nh = ctypes.c_int64(), ctypes.c_int64()
+        ws = self.workspace(n, params)
+        self.check(lib().vr_core_search(self.h, _ptr(pos), _ptr(vel), n, _ptr(label),
+                                        _ptr(label6) if label6 is not None else None, float(lx),
+                                        float(alpha_v), ctypes.byref(params), ctypes.byref(cores),
+                                        _ptr(out["core"]), _ptr(out["level"]), ctypes.byref(nc),
+                                        _ptr(out["halos"]), ctypes.byref(nh), _ptr(ws), ws.numel(),
+                                        _stream(stream)))
+        out["ncores"], out["nhalo"] = nc.value, nh.value
+        return out
 
     def clean_groups(self, ell, label6, params: Params | None = None, beta: float = 1.0,
                      stream=None):
