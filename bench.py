@@ -15,8 +15,8 @@ the slowest rank's time. Rank 0 prints one JSON line.
 The headline runs the batched form (each stage one launch over all halos); the same
 inputs are then timed in the plain form (each stage launched once per halo) and reported
 under "plain_form". Field 6DFOF of the 3DFOF halos, the significance cleaning of the
-step's outlier groups and their two-stage growth are timed afterwards on the same box and
-reported under "next_rows" (outside the headline).
+step's outlier groups, their two-stage growth and the core search are timed afterwards on
+the same box and reported under "next_rows" (outside the headline).
 
 --impl reference times the FP64 C oracle (the path's reference implementation) on the
 host cores, one step = the oracle pipeline over a bounded sample of the workload (a 64^3
@@ -273,8 +273,8 @@ def run_ours(args):
 
     # ---- rows beyond the headline step, on the same box (timed separately, 3 calls each):
     #      field 6DFOF of the 3DFOF halos (Sec. 2.1), significance cleaning of the outlier
-    #      groups the step produced (Sec. 2.2, Eq. ellsig) and their two-stage growth with
-    #      the merge threshold (Sec. 2.2)
+    #      groups the step produced (Sec. 2.2, Eq. ellsig), their two-stage growth with
+    #      the merge threshold (Sec. 2.2) and the core search (Sec. 2.3, Eq. coreloop)
     next_rows = None
     if args.next_rows:
         lx = 0.2 * synth.mean_spacing(box.n)
@@ -299,12 +299,20 @@ def run_ours(args):
             l6g.copy_(out["label6"])
             ctx.grow_groups(pos, vel, out["ell"], lab, hs_g, l6g, P, gp)
 
+        core_out = {}
+
+        def cores():
+            core_out.update(ctx.core_search(pos, vel, lab, out["label6"], lx, 1.25, P,
+                                            out=core_out or None))
+
         field()
         clean()
         grow()
+        cores()
         ctx.sync()
         res = {}
-        for name, f in (("field_6dfof", field), ("clean_groups", clean), ("two_stage_linking", grow)):
+        for name, f in (("field_6dfof", field), ("clean_groups", clean), ("two_stage_linking", grow),
+                        ("core_search", cores)):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize(dev)
             e0.record(stream)
@@ -331,6 +339,11 @@ def run_ours(args):
             "groups_before": int(len(np.unique(a6[a6 >= 0]))),
             "groups_after": int(len(np.unique(ag[ag >= 0]))),
             "gamma": [gp.gamma_ell, gp.gamma_x, gp.gamma_vr, gp.gamma_theta], "f_merge": gp.f_merge})
+        cc = core_out["core"].cpu().numpy()
+        res["core_search"].update({"cores": int(core_out["ncores"]),
+                                   "particles_in_cores": int((cc >= 0).sum()),
+                                   "params": "alpha_x,C 0.8, alpha_v,C 1.0, n_loop 5, f_C 0.02, "
+                                             "alpha_N,C 1.2; l_x 0.2 spacing, l_v 1.25 sigma_v"})
         next_rows = res
 
     # ---- the other launch form on the same inputs: one launch per halo and stage
