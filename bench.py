@@ -47,6 +47,8 @@ WORKLOADS = {
             "l_v = 1.0 sigma_host",
     "c256": "256^3 clustered box, 100 Mpc/h, same generator and parameters as the 512^3 box",
     "m160": "160^3 box (4.1M particles), same generator and parameters: small profiling case",
+    "c1024": "1024^3 clustered box (1.07 B particles), 1 Gpc/h, same generator and parameters "
+             "as the 512^3 box",
 }
 SAMPLE_BOX = "m64"
 SAMPLE_DESC = ("64^3 box (262,144 particles) drawn by the same generator with the same "

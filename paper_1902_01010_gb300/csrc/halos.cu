@@ -206,17 +206,37 @@ SegBufs seg_carve(Arena &ar, int64_t n, int nmin) {
 
 }  // namespace
 
+// The segmentation's outputs, kept for the later stages.
+static void seg_keep(Arena &ar, int64_t n, int nmin, HaloSeg *g) {
+  int64_t hmax = n / (nmin > 0 ? nmin : 1) + 2;
+  uint32_t *hoff = ar.take<uint32_t>(hmax + 1);
+  uint32_t *hlabel = ar.take<uint32_t>(hmax);
+  uint32_t *horder = ar.take<uint32_t>(hmax);
+  uint32_t *hid = ar.take<uint32_t>(n);
+  int4 *u = ar.take<int4>(n);
+  float4 *v = ar.take<float4>(n);
+  uint32_t *scr = ar.take<uint32_t>(n + 1);
+  if (g) {
+    g->hoff = hoff;
+    g->hlabel = hlabel;
+    g->horder = horder;
+    g->hid = hid;
+    g->u = u;
+    g->v = v;
+    g->scratch_u32_a = scr;
+  }
+}
+
 size_t halo_seg_bytes(int64_t n, int nmin) {
   Arena ar;
-  int64_t hmax = n / (nmin > 0 ? nmin : 1) + 2;
-  ar.take<uint32_t>(hmax + 1);  // hoff
-  ar.take<uint32_t>(hmax);      // hlabel
-  ar.take<uint32_t>(hmax);      // horder
-  ar.take<uint32_t>(n);         // hid
-  ar.take<int4>(n);             // u
-  ar.take<float4>(n);           // v
-  seg_carve(ar, n, nmin);
+  seg_keep(ar, n, nmin, nullptr);
   return ar.off;
+}
+
+size_t halo_seg_temp_bytes(int64_t n, int nmin) {
+  Arena ar;
+  seg_carve(ar, n, nmin);
+  return ar.off + 256;
 }
 
 vr_status build_halos(vr_ctx *ctx, const int32_t *pos, const float *vel, int64_t n,
@@ -224,17 +244,16 @@ vr_status build_halos(vr_ctx *ctx, const int32_t *pos, const float *vel, int64_t
                       HaloSeg *out) {
   HaloSeg &g = *out;
   g.n = n;
-  int64_t hmax = n / (nmin > 0 ? nmin : 1) + 2;
-  g.hoff = ar.take<uint32_t>(hmax + 1);
-  g.hlabel = ar.take<uint32_t>(hmax);
-  g.horder = ar.take<uint32_t>(hmax);
-  g.hid = ar.take<uint32_t>(n);
-  g.u = ar.take<int4>(n);
-  g.v = ar.take<float4>(n);
+  seg_keep(ar, n, nmin, &g);
+  // the build buffers below are released when this call returns (later stages reuse them)
+  const size_t keep = ar.off;
   SegBufs B = seg_carve(ar, n, nmin);
-  g.scratch_u32_a = B.cnt;
-  g.scratch_u32_b = B.flag;
   if (!ar.ok()) return set_error(ctx, VR_ERR_WORKSPACE_TOO_SMALL, "workspace too small");
+  struct Release {
+    Arena &a;
+    size_t off;
+    ~Release() { a.off = off; }
+  } release{ar, keep};
   const int T = 256;
   VR_CUDA(ctx, cudaMemsetAsync(B.cnt, 0, (n + 1) * sizeof(uint32_t), s));
   k_count<<<grid_for(n, T), T, 0, s>>>(label, n, B.cnt, ctx->d_status);

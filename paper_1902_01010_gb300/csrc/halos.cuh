@@ -19,14 +19,15 @@ struct HaloSeg {
   uint32_t *hid;       // [NHP] halo of each slot
   int4 *u;             // [NHP] unwrapped position (x, y, z) and local index w
   float4 *v;           // [NHP] velocity (x, y, z) and particle index (w, as int bits)
-  // work arrays kept for later stages
+  // work array kept for later stages
   uint32_t *scratch_u32_a;  // [n + 1]
-  uint32_t *scratch_u32_b;  // [n + 1]
 };
 
 // Carves and builds the segmentation (one stream synchronisation to read H and NHP).
-// The arena must have room for halo_seg_bytes(n, nmin).
+// The outputs take halo_seg_bytes(n, nmin) and stay; the build needs a further
+// halo_seg_temp_bytes(n, nmin), released (arena offset restored) on return.
 size_t halo_seg_bytes(int64_t n, int nmin);
+size_t halo_seg_temp_bytes(int64_t n, int nmin);
 vr_status build_halos(vr_ctx *ctx, const int32_t *pos, const float *vel, int64_t n,
                       const int32_t *label, int nmin, int nsmall, Arena &ar, cudaStream_t s,
                       HaloSeg *out);

@@ -14,6 +14,8 @@ size_t ws_substructure(int64_t n, const vr_params *p) {
   size_t a = velden_bytes(n, p->nmin), b = background_bytes(n, p), c = fof6d_bytes(n, p->nmin);
   size_t m = a > b ? a : b;
   m = m > c ? m : c;
+  const size_t t = halo_seg_temp_bytes(n, p->nmin);
+  m = m > t ? m : t;
   const size_t cl = clean_bytes(n), gr = grow_bytes(n, p->nmin), co = cores_bytes(n, p->nmin);
   m = m > cl ? m : cl;
   m = m > gr ? m : gr;
