@@ -92,6 +92,9 @@ def _lib_():
                                             ctypes.c_int, ctypes.c_int, vp, dbl, vp]),
             "or_core_search": (i64, [vp, vp, vp, i64, vp, dbl, dbl, dbl, dbl, ctypes.c_int,
                                      dbl, dbl, i32, vp, vp]),
+            "or_core_assign": (ctypes.c_int, [vp, i64, vp, ctypes.c_int, ctypes.c_int, vp]),
+            "or_core_grow": (i64, [vp, vp, vp, i64, vp, dbl, dbl, dbl, dbl, ctypes.c_int,
+                                   dbl, dbl, i32, dbl, ctypes.c_int, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -329,6 +332,62 @@ def core_search(pos, vel, label3, label6, lx, alpha_v=1.25, nsearch_min=160, nmi
         core[m] = c
         lev[m] = l
     return core, lev
+
+
+GROW_DEFAULTS = dict(beta_c=1.0, mode=2)  # Table 1 beta_C; Table A1 core growth mode
+
+
+def core_assign(X, init, ncore, mode=2):
+    """One core-growth assignment step (Eq. coredist; mode 0: scalar dispersions) of the
+    phase-space rows X [n][6]: init[i] is the core seeded by row i or -1. Returns (core per
+    row, number of cores with a positive-definite tensor)."""
+    X = _c(X, np.float64)
+    init = _c(init, np.int32)
+    out = np.empty(len(init), np.int32)
+    npd = _lib_().or_core_assign(_p(X), len(init), _p(init), int(ncore), int(mode), _p(out))
+    return out, int(npd)
+
+
+def core_grow_halo(upos, vel, members, lab6, lx, lv, ax=0.8, av=1.0, n_loop=5, f_c=0.02,
+                   an=1.2, nmin=20, beta_c=1.0, mode=2):
+    """Core search, core cleaning (Eq. coresig) and core growth (Eqs. coremeanphase,
+    coredispphase, coredist) inside one halo (Sec. 2.3). Returns (core, level, grown, gap)
+    per member and the number of cores kept; gap is the second smallest D^2 minus the
+    smallest for members assigned by distance, NaN otherwise."""
+    upos = _c(upos, np.int64)
+    vel = _c(vel, np.float32)
+    members = _c(members, np.int32)
+    nh = members.shape[0]
+    l6 = None if lab6 is None else _c(lab6, np.int32)
+    core = np.empty(nh, np.int32)
+    lev = np.empty(nh, np.int32)
+    grown = np.empty(nh, np.int32)
+    gap = np.empty(nh, np.float64)
+    nk = _lib_().or_core_grow(_p(upos), _p(vel), _p(members), nh, _p(l6), float(lx), float(lv),
+                              ax, av, n_loop, f_c, an, nmin, float(beta_c), int(mode), _p(core),
+                              _p(lev), _p(grown), _p(gap))
+    return core, lev, grown, gap, int(nk)
+
+
+def core_grow(pos, vel, label3, label6, lx, alpha_v=1.25, nsearch_min=160, nmin=20, **kw):
+    """core_grow_halo over every halo with N_H >= nsearch_min, lv = alpha_v sigma_v.
+    Returns (core, level, grown, gap) per particle."""
+    n = len(pos)
+    core = np.full(n, -1, np.int32)
+    lev = np.full(n, -1, np.int32)
+    grown = np.full(n, -1, np.int32)
+    gap = np.full(n, np.nan)
+    off, mem = halos(label3, nmin)
+    for h in range(len(off) - 1):
+        m = mem[off[h]:off[h + 1]]
+        if len(m) < nsearch_min:
+            continue
+        lv = alpha_v * halo_frame(vel, m)[3]
+        c, l, g, d, _ = core_grow_halo(unwrap(pos, m), vel, m,
+                                       None if label6 is None else np.asarray(label6, np.int32)[m],
+                                       lx, lv, nmin=nmin, **kw)
+        core[m], lev[m], grown[m], gap[m] = c, l, g, d
+    return core, lev, grown, gap
 
 
 def ell_bar(ell_th: float) -> float:

@@ -1185,11 +1185,17 @@ int or_grow_halo(const int64_t *upos, const float *vel, const int32_t *members, 
  * Labels are the minimum particle index of each core.
  *   out_core [nh]: core label of each member, -1 if none; out_level [nh]: its level.
  * Returns the number of cores (candidate cores + the primary core). */
-int64_t or_core_search(const int64_t *upos, const float *vel, const int32_t *members,
-                       int64_t nh, const int32_t *lab6, double lx, double lv, double ax,
-                       double av, int n_loop, double f_c, double an, int32_t nmin,
-                       int32_t *out_core, int32_t *out_level) {
-  for (int64_t i = 0; i < nh; ++i) { out_core[i] = -1; out_level[i] = -1; }
+/* The loop itself. Besides the outputs above it gives, per member, the last loop at which
+ * it was in the searched background (searched[i], -1 if never), and the primary core's
+ * label and level (-1 if the halo found no group). */
+static int64_t or_core_loop(const int64_t *upos, const float *vel, const int32_t *members,
+                            int64_t nh, const int32_t *lab6, double lx, double lv, double ax,
+                            double av, int n_loop, double f_c, double an, int32_t nmin,
+                            int32_t *out_core, int32_t *out_level, int32_t *searched,
+                            int32_t *prim_label, int32_t *prim_lev) {
+  for (int64_t i = 0; i < nh; ++i) { out_core[i] = -1; out_level[i] = -1; searched[i] = -1; }
+  *prim_label = -1;
+  *prim_lev = -1;
   if (nh <= 0) return 0;
   uint8_t *bg = (uint8_t *)malloc((size_t)nh);
   int32_t *l6 = (int32_t *)malloc((size_t)nh * sizeof(int32_t));
@@ -1201,6 +1207,8 @@ int64_t or_core_search(const int64_t *upos, const float *vel, const int32_t *mem
   for (int l = 0; l < n_loop; ++l) {
     if (l > 0) { lxl = lxl * ax; lvl = lvl * av; thr = thr * an; }
     double prm[5] = {lxl * lxl, lvl * lvl, 0.0, 0.0, 0.0};
+    for (int64_t i = 0; i < nh; ++i)
+      if (bg[i]) searched[i] = l;
     or_fof6d_halo(upos, vel, members, nh, bg, prm, 0.0, 0.0, 1, 0, 1, l6);
     /* group sizes by label slot (labels are member indices: the slot of a label) */
     for (int64_t i = 0; i < nh; ++i) size[i] = 0;
@@ -1230,11 +1238,273 @@ int64_t or_core_search(const int64_t *upos, const float *vel, const int32_t *mem
     for (int64_t i = 0; i < nh; ++i)
       if (bg[i]) { out_core[i] = members[prim]; out_level[i] = prim_level; }
     ncore++;
+    *prim_label = members[prim];
+    *prim_lev = prim_level;
   }
   free(size);
   free(l6);
   free(bg);
   return ncore;
+}
+
+int64_t or_core_search(const int64_t *upos, const float *vel, const int32_t *members,
+                       int64_t nh, const int32_t *lab6, double lx, double lv, double ax,
+                       double av, int n_loop, double f_c, double an, int32_t nmin,
+                       int32_t *out_core, int32_t *out_level) {
+  int32_t *searched = (int32_t *)malloc((size_t)(nh > 0 ? nh : 1) * sizeof(int32_t));
+  int32_t pl, pv;
+  int64_t nc = or_core_loop(upos, vel, members, nh, lab6, lx, lv, ax, av, n_loop, f_c, an, nmin,
+                            out_core, out_level, searched, &pl, &pv);
+  free(searched);
+  return nc;
+}
+
+/* ------------------------------------------- core growth (Sec. 2.3, growth) */
+
+/* Phase-space mean and dispersion tensor (Eqs. coremeanphase, coredispphase) of the
+ * rows i of X [n][6] with sel[i] != 0, unit masses (M = their count): mean = sum X / M,
+ * then S_ab = sum (X_a - mean_a)(X_b - mean_b) / M, both summed in row order. S is a
+ * full row-major 6x6. Returns M (mean and S untouched when M = 0). */
+static int64_t or_phase_moments(const double *X, int64_t n, const uint8_t *sel, double *mean,
+                                double *S) {
+  int64_t m = 0;
+  double sum[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t i = 0; i < n; ++i) {
+    if (!sel[i]) continue;
+    for (int a = 0; a < 6; ++a) sum[a] += X[6 * i + a];
+    m++;
+  }
+  if (m == 0) return 0;
+  for (int a = 0; a < 6; ++a) mean[a] = sum[a] / (double)m;
+  double c[36];
+  for (int a = 0; a < 36; ++a) c[a] = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (!sel[i]) continue;
+    double d[6];
+    for (int a = 0; a < 6; ++a) d[a] = X[6 * i + a] - mean[a];
+    for (int a = 0; a < 6; ++a)
+      for (int b = 0; b < 6; ++b) c[6 * a + b] += d[a] * d[b];
+  }
+  for (int a = 0; a < 36; ++a) S[a] = c[a] / (double)m;
+  return m;
+}
+
+/* Cholesky L L^T = S of a symmetric 6x6 (row-major; the lower triangle is read), L
+ * row-major lower triangular. Returns 0 when a pivot is not > 0 (S not positive
+ * definite, or NaN). */
+static int or_chol6(const double *S, double *L) {
+  for (int a = 0; a < 36; ++a) L[a] = 0.0;
+  for (int j = 0; j < 6; ++j) {
+    double d = S[6 * j + j];
+    for (int k = 0; k < j; ++k) d -= L[6 * j + k] * L[6 * j + k];
+    if (!(d > 0.0)) return 0;
+    const double ljj = sqrt(d);
+    L[6 * j + j] = ljj;
+    for (int i = j + 1; i < 6; ++i) {
+      double t = S[6 * i + j];
+      for (int k = 0; k < j; ++k) t -= L[6 * i + k] * L[6 * j + k];
+      L[6 * i + j] = t / ljj;
+    }
+  }
+  return 1;
+}
+
+/* Eq. coredist: D^2 = d^T S^-1 d with S = L L^T, by forward substitution L y = d and
+ * D^2 = y . y. */
+static double or_dist6(const double *L, const double *d) {
+  double y[6], D2 = 0.0;
+  for (int i = 0; i < 6; ++i) {
+    double t = d[i];
+    for (int k = 0; k < i; ++k) t -= L[6 * i + k] * y[k];
+    y[i] = t / L[6 * i + i];
+    D2 += y[i] * y[i];
+  }
+  return D2;
+}
+
+/* Distance of X to a core (mean, S, L) under growth mode `mode`: modes 1 and 2 use
+ * Eq. coredist; mode 0 uses the scalar form D^2 = |x - xbar|^2 / s_x^2 + |v - vbar|^2 / s_v^2
+ * with s_x^2 = (S_xx + S_yy + S_zz) / 3 and s_v^2 = (S_vxvx + S_vyvy + S_vzvz) / 3. +inf
+ * for a core whose tensor is not positive definite. */
+static double or_core_d2(int mode, const double *mean, const double *S, const double *L, int pd,
+                         const double *X) {
+  double d[6];
+  for (int a = 0; a < 6; ++a) d[a] = X[a] - mean[a];
+  if (!pd) return INFINITY;
+  if (mode != 0) return or_dist6(L, d);
+  const double sx2 = (S[0] + S[7] + S[14]) / 3.0, sv2 = (S[21] + S[28] + S[35]) / 3.0;
+  return (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) / sx2 +
+         (d[3] * d[3] + d[4] * d[4] + d[5] * d[5]) / sv2;
+}
+
+/* One assignment step of core growth on given points (Sec. 2.3, Eqs. coremeanphase,
+ * coredispphase, coredist; the paper's Gaussian-mixture comparison): X [n][6] phase-space
+ * points, init[i] the core (0 .. ncore - 1) that point i seeds or -1. Every core's mean
+ * and tensor come from its seed points; every unseeded point goes to the core of
+ * smallest D^2 under `mode` (or_core_d2; ties: the smaller core; -1 if no core is
+ * finite); seeds keep their core. Returns the number of cores whose tensor is positive
+ * definite. */
+int or_core_assign(const double *X, int64_t n, const int32_t *init, int ncore, int mode,
+                   int32_t *out) {
+  double *mean = (double *)malloc((size_t)(ncore > 0 ? ncore : 1) * 6 * sizeof(double));
+  double *S = (double *)malloc((size_t)(ncore > 0 ? ncore : 1) * 36 * sizeof(double));
+  double *L = (double *)malloc((size_t)(ncore > 0 ? ncore : 1) * 36 * sizeof(double));
+  int *pd = (int *)malloc((size_t)(ncore > 0 ? ncore : 1) * sizeof(int));
+  uint8_t *sel = (uint8_t *)malloc((size_t)(n > 0 ? n : 1));
+  int npd = 0;
+  for (int c = 0; c < ncore; ++c) {
+    for (int64_t i = 0; i < n; ++i) sel[i] = init[i] == c;
+    pd[c] = or_phase_moments(X, n, sel, mean + 6 * c, S + 36 * c) > 0 &&
+            or_chol6(S + 36 * c, L + 36 * c);
+    npd += pd[c];
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    out[i] = init[i];
+    if (init[i] >= 0) continue;
+    double best = INFINITY;
+    for (int c = 0; c < ncore; ++c) {
+      const double D2 = or_core_d2(mode, mean + 6 * c, S + 36 * c, L + 36 * c, pd[c], X + 6 * i);
+      if (D2 < best) { best = D2; out[i] = c; }
+    }
+  }
+  free(sel); free(pd); free(L); free(S); free(mean);
+  return npd;
+}
+
+/* Core search followed by core cleaning and core growth inside one halo (Sec. 2.3,
+ * "Core Growth & Mass Reconstruction" and "Cleaning the Catalogue"; Eqs. coremeanphase,
+ * coredispphase, coredist, coresig). The search is or_core_search's. Then:
+ *  - cores: the candidate cores of every level and the primary core, each with its
+ *    members at the end of the search;
+ *  - cleaning (Eq. coresig): candidate core n of level l_n is kept iff
+ *    D^2(mean_p -> core n) >= beta_c, with core n's own tensor and mean_p the mean of the
+ *    primary group of level l_n (the largest group of that loop: the members searched
+ *    at loop l_n + 1, plus the final primary core). A core whose tensor is not positive
+ *    definite is dropped. A dropped core's members return to the untagged background;
+ *  - growth, only when at least one candidate core is kept: for l = n_loop - 1 down to 0,
+ *    the active cores are the primary core and the kept candidate cores of level >= l;
+ *    every untagged member that was last searched at loop l is assigned to the active
+ *    core of smallest D^2 (ties: the smaller label; cores whose tensor is not positive
+ *    definite are skipped), all members of one level against the tensors held at the
+ *    start of that level. Mode 2 (Table A1 default) recomputes every active core's
+ *    mean and tensor from its current members at the start of each level, mode 1 keeps
+ *    the tensors of the cores as found, mode 0 uses the scalar form of or_core_d2.
+ *   out_core, out_level: as or_core_search; out_grown [nh]: the core label of each
+ *   member after cleaning and growth, -1 for none; out_gap [nh] (may be NULL): for a
+ *   member assigned by distance, the second smallest D^2 minus the smallest (+inf if
+ *   one core was finite), else NaN.
+ * Returns the number of cores kept (kept candidate cores + the primary core). */
+int64_t or_core_grow(const int64_t *upos, const float *vel, const int32_t *members, int64_t nh,
+                     const int32_t *lab6, double lx, double lv, double ax, double av, int n_loop,
+                     double f_c, double an, int32_t nmin, double beta_c, int mode,
+                     int32_t *out_core, int32_t *out_level, int32_t *out_grown, double *out_gap) {
+  const size_t nb = (size_t)(nh > 0 ? nh : 1);
+  int32_t *searched = (int32_t *)malloc(nb * sizeof(int32_t));
+  int32_t prim_label, prim_lev;
+  or_core_loop(upos, vel, members, nh, lab6, lx, lv, ax, av, n_loop, f_c, an, nmin, out_core,
+               out_level, searched, &prim_label, &prim_lev);
+  for (int64_t i = 0; i < nh; ++i) {
+    out_grown[i] = out_core[i];
+    if (out_gap) out_gap[i] = NAN;
+  }
+  if (prim_label < 0) { free(searched); return 0; }
+  double *X = (double *)malloc(nb * 6 * sizeof(double));  /* (x, y, z, vx, vy, vz) rows */
+  for (int64_t i = 0; i < nh; ++i) {
+    const float *v = vel + 3 * (int64_t)members[i];
+    for (int a = 0; a < 3; ++a) {
+      X[6 * i + a] = (double)upos[3 * i + a];
+      X[6 * i + 3 + a] = (double)v[a];
+    }
+  }
+  /* cores, in increasing label order: a core's label is its minimum member index, so
+   * its root is the member whose own index is the label */
+  int64_t nc = 0;
+  for (int64_t i = 0; i < nh; ++i)
+    if (out_core[i] == members[i]) nc++;
+  int32_t *clab = (int32_t *)malloc((size_t)nc * sizeof(int32_t));
+  int32_t *clev = (int32_t *)malloc((size_t)nc * sizeof(int32_t));
+  uint8_t *alive = (uint8_t *)malloc((size_t)nc);
+  double *cmean = (double *)malloc((size_t)nc * 6 * sizeof(double));
+  double *cS = (double *)malloc((size_t)nc * 36 * sizeof(double));
+  double *cL = (double *)malloc((size_t)nc * 36 * sizeof(double));
+  int *cpd = (int *)malloc((size_t)nc * sizeof(int));
+  int32_t *cur = (int32_t *)malloc(nb * sizeof(int32_t));  /* core index of each member */
+  int32_t *nxt = (int32_t *)malloc(nb * sizeof(int32_t));
+  uint8_t *sel = (uint8_t *)malloc(nb);
+  int64_t k = 0, pc = -1;
+  for (int64_t i = 0; i < nh; ++i)
+    if (out_core[i] == members[i]) {
+      clab[k] = out_core[i];
+      clev[k] = out_level[i];
+      alive[k] = 1;
+      if (out_core[i] == prim_label) pc = k;
+      k++;
+    }
+  for (int64_t i = 0; i < nh; ++i) {
+    cur[i] = -1;
+    if (out_core[i] < 0) continue;
+    int64_t lo = 0, hi = nc;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) / 2;
+      if (clab[mid] < out_core[i]) lo = mid + 1; else hi = mid;
+    }
+    cur[i] = (int32_t)lo;
+  }
+  /* the cores as found (Eqs. coremeanphase, coredispphase) */
+  for (int64_t c = 0; c < nc; ++c) {
+    for (int64_t i = 0; i < nh; ++i) sel[i] = cur[i] == c;
+    or_phase_moments(X, nh, sel, cmean + 6 * c, cS + 36 * c);
+    cpd[c] = or_chol6(cS + 36 * c, cL + 36 * c);
+  }
+  /* cleaning (Eq. coresig) */
+  int64_t kept = 0;
+  for (int64_t c = 0; c < nc; ++c) {
+    if (c == pc) continue;
+    for (int64_t i = 0; i < nh; ++i) sel[i] = searched[i] >= clev[c] + 1 || out_core[i] == prim_label;
+    double mp[6], Sp[36];
+    or_phase_moments(X, nh, sel, mp, Sp);
+    double d[6];
+    for (int a = 0; a < 6; ++a) d[a] = mp[a] - cmean[6 * c + a];
+    const int keep = cpd[c] && or_dist6(cL + 36 * c, d) >= beta_c;
+    alive[c] = (uint8_t)keep;
+    kept += keep;
+  }
+  for (int64_t i = 0; i < nh; ++i)
+    if (cur[i] >= 0 && !alive[cur[i]]) cur[i] = -1;
+  if (kept > 0) {
+    for (int l = n_loop - 1; l >= 0; --l) {
+      if (mode == 2)
+        for (int64_t c = 0; c < nc; ++c) {
+          if (!alive[c] || (c != pc && clev[c] < l)) continue;
+          for (int64_t i = 0; i < nh; ++i) sel[i] = cur[i] == c;
+          or_phase_moments(X, nh, sel, cmean + 6 * c, cS + 36 * c);
+          cpd[c] = or_chol6(cS + 36 * c, cL + 36 * c);
+        }
+      for (int64_t i = 0; i < nh; ++i) {
+        nxt[i] = cur[i];
+        if (cur[i] >= 0 || searched[i] != l) continue;
+        double b1 = INFINITY, b2 = INFINITY;
+        int64_t bc = -1;
+        for (int64_t c = 0; c < nc; ++c) {  /* increasing labels: ties keep the smaller */
+          if (!alive[c] || (c != pc && clev[c] < l)) continue;
+          const double D2 =
+              or_core_d2(mode, cmean + 6 * c, cS + 36 * c, cL + 36 * c, cpd[c], X + 6 * i);
+          if (!(D2 < INFINITY)) continue;
+          if (bc < 0 || D2 < b1) { b2 = b1; b1 = D2; bc = c; }
+          else if (D2 < b2) b2 = D2;
+        }
+        if (bc >= 0) {
+          nxt[i] = (int32_t)bc;
+          if (out_gap) out_gap[i] = b2 - b1;
+        }
+      }
+      for (int64_t i = 0; i < nh; ++i) cur[i] = nxt[i];
+    }
+  }
+  for (int64_t i = 0; i < nh; ++i) out_grown[i] = cur[i] >= 0 ? clab[cur[i]] : -1;
+  free(sel); free(nxt); free(cur); free(cpd); free(cL); free(cS); free(cmean); free(alive);
+  free(clev); free(clab); free(X); free(searched);
+  return kept + 1;
 }
 
 /* ------------------------------------------------------- field 6DFOF (Sec. 2.1) */
