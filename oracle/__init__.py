@@ -334,7 +334,7 @@ def core_search(pos, vel, label3, label6, lx, alpha_v=1.25, nsearch_min=160, nmi
     return core, lev
 
 
-GROW_DEFAULTS = dict(beta_c=1.0, mode=2)  # Table 1 beta_C; Table A1 core growth mode
+CORE_GROW_DEFAULTS = dict(beta_c=1.0, mode=2)  # Table 1 beta_C; Table A1 core growth mode
 
 
 def core_assign(X, init, ncore, mode=2):
