@@ -276,7 +276,8 @@ def run_ours(args):
     # ---- rows beyond the headline step, on the same box (timed separately, 3 calls each):
     #      field 6DFOF of the 3DFOF halos (Sec. 2.1), significance cleaning of the outlier
     #      groups the step produced (Sec. 2.2, Eq. ellsig), their two-stage growth with
-    #      the merge threshold (Sec. 2.2) and the core search (Sec. 2.3, Eq. coreloop)
+    #      the merge threshold (Sec. 2.2), the core search (Sec. 2.3, Eq. coreloop) and the
+    #      core search followed by core cleaning and growth (Sec. 2.3, Eqs. coresig, coredist)
     next_rows = None
     if args.next_rows:
         lx = 0.2 * synth.mean_spacing(box.n)
@@ -307,14 +308,21 @@ def run_ours(args):
             core_out.update(ctx.core_search(pos, vel, lab, out["label6"], lx, 1.25, P,
                                             out=core_out or None))
 
+        grow_out = {}
+
+        def core_growth():
+            grow_out.update(ctx.core_grow(pos, vel, lab, out["label6"], lx, 1.25, P,
+                                          out=grow_out or None))
+
         field()
         clean()
         grow()
         cores()
+        core_growth()
         ctx.sync()
         res = {}
         for name, f in (("field_6dfof", field), ("clean_groups", clean), ("two_stage_linking", grow),
-                        ("core_search", cores)):
+                        ("core_search", cores), ("core_search_and_growth", core_growth)):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize(dev)
             e0.record(stream)
@@ -346,6 +354,12 @@ def run_ours(args):
                                    "particles_in_cores": int((cc >= 0).sum()),
                                    "params": "alpha_x,C 0.8, alpha_v,C 1.0, n_loop 5, f_C 0.02, "
                                              "alpha_N,C 1.2; l_x 0.2 spacing, l_v 1.25 sigma_v"})
+        gg, gc = grow_out["grown"].cpu().numpy(), grow_out["core"].cpu().numpy()
+        res["core_search_and_growth"].update({
+            "cores_kept": int(grow_out["nkept"]), "particles_in_cores": int((gc >= 0).sum()),
+            "particles_in_grown_cores": int((gg >= 0).sum()),
+            "params": "core search as core_search; beta_C 1, growth mode 2 (tensors "
+                      "recomputed per level)"})
         next_rows = res
 
     # ---- the other launch form on the same inputs: one launch per halo and stage

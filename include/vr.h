@@ -272,6 +272,56 @@ vr_status vr_core_search(vr_ctx *ctx, const int32_t *pos, const float *vel, int6
                          int32_t *level, int64_t *ncores, double *halo_stats, int64_t *nhalo,
                          void *ws, size_t ws_bytes, void *stream);
 
+/* Core cleaning and core growth (Sec. 2.3, "Cleaning the Catalogue" and "Core Growth &
+ * Mass Reconstruction"; Eqs. coremeanphase, coredispphase, coredist, coresig), run
+ * after the core search of vr_core_search inside every searched halo. Phase-space
+ * points are X = (x, y, z, vx, vy, vz): the member's position unwrapped about the halo
+ * (lattice units) and its velocity. A core's mean and dispersion tensor are the plain
+ * mean and 1/M second moment of its members' X (unit masses), its distance
+ * D^2 = (X - mean)^T Sigma^-1 (X - mean) (Eq. coredist).
+ *  - Cleaning (Eq. coresig): a candidate core n of level l_n is kept iff
+ *    D^2(mean_p) >= beta_c under core n's tensor, mean_p the mean of the primary group
+ *    of loop l_n (the members searched at loop l_n + 1 plus the final primary core). A
+ *    core whose tensor is not positive definite is dropped; a dropped core's members
+ *    return to the untagged background.
+ *  - Growth, in halos that keep a candidate core: for l = n_loop - 1 down to 0, every
+ *    untagged member last searched at loop l goes to the active core (the primary core
+ *    and the kept candidate cores of level >= l) of smallest D^2, ties to the smaller
+ *    label, cores without a positive-definite tensor skipped; all members of a level
+ *    use the tensors held at the start of that level.
+ *  - mode (Table A1, Use_phase_tensor_core_growth): 2 = every active core's mean and
+ *    tensor recomputed from its current members at each level (default); 1 = the
+ *    tensors of the cores as found; 0 = the scalar form D^2 = |x - xbar|^2 / s_x^2 +
+ *    |v - vbar|^2 / s_v^2, s_x^2 and s_v^2 the mean diagonal of the position and velocity
+ *    blocks of the core as found (the paper prints this form without squares; read as
+ *    squared).
+ * Means and tensors are FP64 sums in an order of the library's choosing, so a D^2 can
+ * differ from a sequential sum in its last bits: an assignment whose two smallest D^2
+ * differ by a few ulp may go either way. Table 1 / A1 defaults
+ * (vr_core_grow_params_default): beta_c = 1, mode = 2. */
+typedef struct {
+  double beta_c;  /* significance beta_C of Eq. coresig */
+  int32_t mode;   /* 0, 1 or 2, as above */
+} vr_core_grow_params;
+
+void vr_core_grow_params_default(vr_core_grow_params *g);
+
+/*   pos .. level, halo_stats, nhalo: as for vr_core_search (same outputs)
+ *   grown      int32 [n] out: the core label of each particle after cleaning and growth,
+ *              -1 for none (substructure members, members of halos that were not
+ *              searched, untagged members of halos without growth)
+ *   nkept      int64 host pointer out (may be NULL): cores kept (kept candidate cores +
+ *              primary cores)
+ * Workspace: vr_workspace_size. This call synchronises `stream`. Errors:
+ * VR_ERR_INVALID_ARG for the core-search parameter checks, beta_c < 0 or NaN, or a mode
+ * other than 0, 1, 2. */
+vr_status vr_core_grow(vr_ctx *ctx, const int32_t *pos, const float *vel, int64_t n,
+                       const int32_t *label, const int32_t *label6, double lx, double alpha_v,
+                       const vr_params *p, const vr_core_params *cp, const vr_core_grow_params *gp,
+                       int32_t *core, int32_t *level, int32_t *grown, int64_t *nkept,
+                       double *halo_stats, int64_t *nhalo, void *ws, size_t ws_bytes,
+                       void *stream);
+
 /* Cleaning of outlier groups (Sec. 2.2, "Cleaning the catalogue", Eq. ellsig). A group
  * of N particles (equal labels >= 0 in label6) is significant iff
  *   <ell> >= ell_bar(p->ell_th) (1 + beta/sqrt(N)),

@@ -17,7 +17,7 @@
 
 #include <vector>
 
-#include "halos.cuh"
+#include "stages.h"
 #include "vr_workspace.h"
 #include "unionfind.cuh"
 
@@ -629,6 +629,17 @@ __global__ void k_core_halos(int64_t H, const unsigned long long *__restrict__ b
   prim[h] = (int)(~(uint32_t)best[h]);
 }
 
+// Loop l: the members of a searching halo's background were searched at l.
+__global__ void k_core_searched(const uint32_t *__restrict__ hid, const float4 *__restrict__ v,
+                                int64_t nhp, const uint8_t *__restrict__ mask,
+                                const int *__restrict__ active, int l,
+                                int32_t *__restrict__ searched) {
+  const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= nhp) return;
+  const int pi = __float_as_int(v[m].w);
+  if (mask[pi] && active[hid[m]]) searched[pi] = l;
+}
+
 // The last primary core of every halo that found one.
 __global__ void k_core_final(const uint32_t *__restrict__ hid, const float4 *__restrict__ v,
                              int64_t nhp, const uint8_t *__restrict__ mask,
@@ -769,7 +780,8 @@ size_t grow_bytes(int64_t n, int nmin) {
 
 vr_status run_cores(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, const vr_core_params *cp,
                     double lx, double alpha_v, Arena &ar, const int32_t *label6, double *hs,
-                    int32_t *core, int32_t *level, int64_t *ncores, cudaStream_t s) {
+                    int32_t *core, int32_t *level, int64_t *ncores, cudaStream_t s,
+                    CoreExtra *ex) {
   if (ncores) *ncores = 0;
   const int64_t H = g.H, n = g.n;
   uint8_t *mask = ar.take<uint8_t>(n);
@@ -784,6 +796,11 @@ vr_status run_cores(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, const vr_
   const int T = 256;
   vr_status st0 = fill_i32(ctx, core, n, -1, s);
   if (st0 == VR_OK) st0 = fill_i32(ctx, level, n, -1, s);
+  if (st0 == VR_OK && ex && ex->searched) st0 = fill_i32(ctx, ex->searched, n, -1, s);
+  if (ex) {
+    ex->prim = prim;
+    ex->last = last;
+  }
   if (st0 != VR_OK || H == 0) return st0;
   VR_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
   k_fill_i32<<<grid_for(H, T), T, 0, s>>>(last, H, -1);
@@ -798,6 +815,11 @@ vr_status run_cores(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, const vr_
                                               cp->f_c, cp->alpha_n, p->nsearch_min, active, lv,
                                               thr, best, hs);
     VR_LAUNCHED(ctx, "k_core_rows");
+    if (ex && ex->searched) {
+      k_core_searched<<<grid_for(g.NHP, T), T, 0, s>>>(g.hid, g.v, g.NHP, mask, active, l,
+                                                        ex->searched);
+      VR_LAUNCHED(ctx, "k_core_searched");
+    }
     ar.off = mark;
     Cands C;
     vr_status st = prep_cands(ctx, g, p->nmin, ar, nullptr, 0.0, nullptr, hs, H, s, &C, mask);

@@ -29,10 +29,28 @@ vr_status run_grow(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, const vr_g
                    Arena &ar, const float *ell, const double *hp, int64_t nhalo, int32_t *label6,
                    cudaStream_t s);
 size_t cores_bytes(int64_t n, int nmin);
+// Optional extra outputs of the core search for core growth: `searched` (caller's device
+// array [n]) gets the last loop at which each particle was in a searching halo's
+// background (-1 if never); `prim` / `last` point to per-halo arrays in the arena (the
+// primary core's label and level, -1 for halos without one), valid while the arena
+// region is not reused.
+struct CoreExtra {
+  int32_t *searched = nullptr;
+  const int *prim = nullptr;
+  const int *last = nullptr;
+};
 // Core search (Eq. coreloop) on a segmentation whose halo rows hold SIGMA.
 vr_status run_cores(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, const vr_core_params *cp,
                     double lx, double alpha_v, Arena &ar, const int32_t *label6, double *hs,
-                    int32_t *core, int32_t *level, int64_t *ncores, cudaStream_t s);
+                    int32_t *core, int32_t *level, int64_t *ncores, cudaStream_t s,
+                    CoreExtra *ex = nullptr);
+size_t coregrow_bytes(int64_t n, int nmin);
+// Core cleaning (Eq. coresig) and core growth (Eqs. coremeanphase-coredist) after
+// run_cores(..., ex): grown [n] out (-1 where no core), *nkept = cores kept.
+vr_status run_core_grow(vr_ctx *ctx, const HaloSeg &g, const vr_core_params *cp,
+                        const vr_core_grow_params *gp, Arena &ar, const int32_t *core,
+                        const int32_t *level, const CoreExtra &ex, int32_t *grown,
+                        int64_t *nkept, cudaStream_t s);
 size_t clean_bytes(int64_t n);
 // Significance cleaning of groups (Eq. ellsig); synchronises the stream.
 vr_status run_clean(vr_ctx *ctx, const float *ell, int64_t n, const vr_params *p, double beta,

@@ -16,7 +16,8 @@ size_t ws_substructure(int64_t n, const vr_params *p) {
   m = m > c ? m : c;
   const size_t t = halo_seg_temp_bytes(n, p->nmin);
   m = m > t ? m : t;
-  const size_t cl = clean_bytes(n), gr = grow_bytes(n, p->nmin), co = cores_bytes(n, p->nmin);
+  const size_t cl = clean_bytes(n), gr = grow_bytes(n, p->nmin),
+               co = cores_bytes(n, p->nmin) + coregrow_bytes(n, p->nmin);
   m = m > cl ? m : cl;
   m = m > gr ? m : gr;
   m = m > co ? m : co;
@@ -207,6 +208,48 @@ vr_status vr_core_search(vr_ctx *ctx, const int32_t *pos, const float *vel, int6
   if ((st = run_halo_frame(ctx, g, p->nsearch_min, halo_stats, s)) != VR_OK) return st;
   if ((st = run_cores(ctx, g, p, cp, lx, alpha_v, ar, label6, halo_stats, core, level, ncores,
                       s)) != VR_OK)
+    return st;
+  if (nhalo) *nhalo = g.H;
+  return read_status(ctx, s, nullptr);
+}
+
+void vr_core_grow_params_default(vr_core_grow_params *g) {
+  if (!g) return;
+  g->beta_c = 1.0;  // Table 1, beta_C
+  g->mode = 2;      // Table A1, Use_phase_tensor_core_growth
+}
+
+vr_status vr_core_grow(vr_ctx *ctx, const int32_t *pos, const float *vel, int64_t n,
+                       const int32_t *label, const int32_t *label6, double lx, double alpha_v,
+                       const vr_params *p, const vr_core_params *cp, const vr_core_grow_params *gp,
+                       int32_t *core, int32_t *level, int32_t *grown, int64_t *nkept,
+                       double *halo_stats, int64_t *nhalo, void *ws, size_t ws_bytes,
+                       void *stream) {
+  if (!ctx) return VR_ERR_INVALID_ARG;
+  vr_status st = common_checks(ctx, n, p);
+  if (st != VR_OK) return st;
+  if (nkept) *nkept = 0;
+  if (nhalo) *nhalo = 0;
+  if (n == 0) return VR_OK;
+  if (!pos || !vel || !label || !cp || !gp || !core || !level || !grown || !halo_stats || !ws)
+    return set_error(ctx, VR_ERR_INVALID_ARG, "NULL pointer");
+  if (!(lx > 0.0) || !(alpha_v > 0.0) || !(cp->alpha_x > 0.0) || !(cp->alpha_v > 0.0) ||
+      cp->n_loop < 0 || cp->n_loop > 1000 || !(cp->f_c >= 0.0) || !(cp->alpha_n > 0.0))
+    return set_error(ctx, VR_ERR_INVALID_ARG, "bad core search parameters");
+  if (!(gp->beta_c >= 0.0) || gp->mode < 0 || gp->mode > 2)
+    return set_error(ctx, VR_ERR_INVALID_ARG, "bad core growth parameters");
+  cudaStream_t s = (cudaStream_t)stream;
+  Arena ar(ws, ws_bytes);
+  HaloSeg g;
+  if ((st = build_halos(ctx, pos, vel, n, label, p->nmin, p->nse, ar, s, &g)) != VR_OK) return st;
+  if ((st = run_halo_frame(ctx, g, p->nsearch_min, halo_stats, s)) != VR_OK) return st;
+  CoreExtra ex;
+  ex.searched = ar.take<int32_t>(n);
+  if (!ar.ok()) return set_error(ctx, VR_ERR_WORKSPACE_TOO_SMALL, "workspace too small");
+  if ((st = run_cores(ctx, g, p, cp, lx, alpha_v, ar, label6, halo_stats, core, level, nullptr,
+                      s, &ex)) != VR_OK)
+    return st;
+  if ((st = run_core_grow(ctx, g, cp, gp, ar, core, level, ex, grown, nkept, s)) != VR_OK)
     return st;
   if (nhalo) *nhalo = g.H;
   return read_status(ctx, s, nullptr);

@@ -26,7 +26,8 @@ H_LABEL, H_NH, H_SEARCHED, H_RBAR, H_SIGR, H_VFX, H_VFY, H_VFZ, H_SIGMA, H_LX2, 
 EXPORTS = ("vr_params_default", "vr_create", "vr_destroy", "vr_last_error", "vr_workspace_size",
            "vr_sync", "vr_fof3d", "vr_velden", "vr_outlier_ratio", "vr_fof6d",
            "vr_fof6d_field", "vr_clean_groups", "vr_grow_params_default", "vr_grow_groups",
-           "vr_core_params_default", "vr_core_search", "vr_find_substructure")
+           "vr_core_params_default", "vr_core_search", "vr_core_grow_params_default",
+           "vr_core_grow", "vr_find_substructure")
 
 
 class VrError(RuntimeError):
@@ -88,6 +89,21 @@ class CoreParams(ctypes.Structure):
         return c
 
 
+class CoreGrowParams(ctypes.Structure):
+    """Mirror of vr_core_grow_params (include/vr.h): beta_C of the cleaning and the
+    growth mode."""
+
+    _fields_ = [("beta_c", ctypes.c_double), ("mode", ctypes.c_int32)]
+
+    @classmethod
+    def default(cls, **kw) -> "CoreGrowParams":
+        g = cls()
+        lib().vr_core_grow_params_default(ctypes.byref(g))
+        for k, v in kw.items():
+            setattr(g, k, v)
+        return g
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -131,6 +147,12 @@ def lib(build_if_missing: bool = True):
                                                   ctypes.POINTER(CoreParams), vp, vp,
                                                   ctypes.POINTER(i64), vp, ctypes.POINTER(i64),
                                                   vp, sz, vp]),
+                "vr_core_grow_params_default": (None, [ctypes.POINTER(CoreGrowParams)]),
+                "vr_core_grow": (ctypes.c_int, [vp, vp, vp, i64, vp, vp, dbl, dbl, P,
+                                                ctypes.POINTER(CoreParams),
+                                                ctypes.POINTER(CoreGrowParams), vp, vp, vp,
+                                                ctypes.POINTER(i64), vp, ctypes.POINTER(i64),
+                                                vp, sz, vp]),
                 "vr_grow_groups": (ctypes.c_int, [vp, vp, vp, vp, i64, vp, vp, i64, P,
                                                   ctypes.POINTER(GrowParams), vp, vp, sz, vp]),
                 "vr_find_substructure": (ctypes.c_int, [vp, vp, vp, i64, vp, dbl, dbl, P,
@@ -302,6 +324,33 @@ class Context:
                                         _ptr(out["halos"]), ctypes.byref(nh), _ptr(ws), ws.numel(),
                                         _stream(stream)))
         out["ncores"], out["nhalo"] = nc.value, nh.value
+        return out
+
+    def core_grow(self, pos, vel, label, label6, lx: float, alpha_v: float = 1.25,
+                  params: Params | None = None, cores: CoreParams | None = None,
+                  grow: CoreGrowParams | None = None, out=None, stream=None):
+        """Core search, core cleaning and core growth (vr_core_grow). label6 may be None.
+        Returns a dict with core, level, grown, nkept, halos (rows) and nhalo."""
+        n = pos.shape[0]
+        params = params or Params.default()
+        cores = cores or CoreParams.default()
+        grow = grow or CoreGrowParams.default()
+        if out is None:
+            dev = pos.device
+            out = dict(core=torch.empty(n, dtype=torch.int32, device=dev),
+                       level=torch.empty(n, dtype=torch.int32, device=dev),
+                       grown=torch.empty(n, dtype=torch.int32, device=dev),
+                       halos=torch.empty((n // max(params.nmin, 1) + 1, HALO_COLS),
+                                         dtype=torch.float64, device=dev))
+        nk, nh = ctypes.c_int64(), ctypes.c_int64()
+        ws = self.workspace(n, params)
+        self.check(lib().vr_core_grow(self.h, _ptr(pos), _ptr(vel), n, _ptr(label),
+                                      _ptr(label6) if label6 is not None else None, float(lx),
+                                      float(alpha_v), ctypes.byref(params), ctypes.byref(cores),
+                                      ctypes.byref(grow), _ptr(out["core"]), _ptr(out["level"]),
+                                      _ptr(out["grown"]), ctypes.byref(nk), _ptr(out["halos"]),
+                                      ctypes.byref(nh), _ptr(ws), ws.numel(), _stream(stream)))
+        out["nkept"], out["nhalo"] = nk.value, nh.value
         return out
 
     def clean_groups(self, ell, label6, params: Params | None = None, beta: float = 1.0,
