@@ -1,7 +1,26 @@
 """Shared test helpers: run the oracle per halo and compare with tolerances."""
+import functools
+
 import numpy as np
 
 import oracle
+import synth
+
+
+@functools.lru_cache(maxsize=2)
+def named_box(name):
+    """synth.named(name), drawn once per test process."""
+    return synth.named(name)
+
+
+@functools.lru_cache(maxsize=2)
+def oracle_labels(name):
+    """Oracle 3D FOF labels of a named box, computed once per test process (the 256^3
+    box takes minutes)."""
+    box = named_box(name)
+    lab = oracle.fof3d(box.pos, box.link_d2)
+    lab.setflags(write=False)
+    return lab
 
 
 def oracle_fl(pos, vel, label, nse=256, nv=32, nmin=20):

@@ -4,6 +4,7 @@ import pytest
 import torch
 
 import oracle
+from helpers import named_box, oracle_labels
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -84,7 +85,7 @@ def test_mass_function_box_64cubed(ctx):
 
 @pytest.mark.slow
 def test_256cubed_bit_exact(ctx):
-    box = synth.named("c256")
+    box = named_box("c256")
     got = _run(ctx, box.pos, box.link_d2)
-    ref = oracle.fof3d(box.pos, box.link_d2)
+    ref = oracle_labels("c256")
     assert np.array_equal(got, ref)

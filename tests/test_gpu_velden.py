@@ -9,7 +9,7 @@ import torch
 
 import oracle
 import synth
-from helpers import assert_close_nan, oracle_fl
+from helpers import assert_close_nan, named_box, oracle_fl, oracle_labels
 
 pytestmark = pytest.mark.gpu
 RTOL = 1e-4
@@ -101,8 +101,8 @@ def test_non_halo_particles_are_nan(ctx):
 def test_256cubed_sampled(ctx):
     """Full 256^3 box in the benchmark's launch form; 3000 sampled members (biased to
     the largest halos) computed one by one by the oracle."""
-    box = synth.named("c256")
-    lab = oracle.fof3d(box.pos, box.link_d2)
+    box = named_box("c256")
+    lab = oracle_labels("c256")
     got = _gpu_fl(ctx, box.pos, box.vel, lab)
     off, mem = oracle.halos(lab, 20)
     sizes = np.diff(off)
