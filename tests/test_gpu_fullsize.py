@@ -1,6 +1,7 @@
-"""The 512^3 clustered box (134M particles, the benchmark's workload) through the
-benchmark's calls and launch form: vr_fof3d, then vr_find_substructure batched, default
-parameters. The oracle cannot run the whole box, so it checks sampled outputs one by one:
+"""The 512^3 clustered box (134M particles, the benchmark's workload) and the 1024^3 box
+(1.07B particles) through the benchmark's calls and launch form: vr_fof3d, then
+vr_find_substructure batched, default parameters. The oracle cannot run a whole box, so
+it checks sampled outputs one by one (group members are gathered on the GPU):
 
   - 3D groups. A sampled group G is recomputed by the oracle's FOF over every particle
     within the linking length of G's bounding box (periodic). That set holds every
@@ -25,21 +26,30 @@ pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 L = 1 << 21
 
 
-@pytest.fixture(scope="module")
-def run():
+@pytest.fixture(scope="module", params=["c512", "c1024"])
+def run(request):
     from paper_1902_01010_gb300 import Context
 
     ctx = Context(0)
-    box = named_box("c512")
+    box = named_box(request.param)
     pos, vel = torch.from_numpy(box.pos).cuda(), torch.from_numpy(box.vel).cuda()
     lab = ctx.fof3d(pos, box.link_d2)
     out = ctx.find_substructure(pos, vel, lab, box.lx_sub, 1.0)
     ctx.sync()
-    res = dict(box=box, pos_t=pos, label=lab.cpu().numpy(), nhalo=out["nhalo"])
+    res = dict(box=box, pos_t=pos, lab_t=lab, label=lab.cpu().numpy(), nhalo=out["nhalo"])
     for k in ("f_l", "R", "ell", "label6"):
         res[k] = out[k].cpu().numpy()
     res["hs"] = out["halos"][: out["nhalo"]].cpu().numpy()
-    return res
+    del out, lab, vel
+    yield res
+    res.clear()
+    del ctx, pos
+    torch.cuda.empty_cache()
+
+
+def _members(r, label):
+    """Particles with 3D label `label`, in increasing index order."""
+    return torch.nonzero(r["lab_t"] == int(label)).squeeze(1).cpu().numpy().astype(np.int32)
 
 
 def _neighbourhood(pos_t, members, pos_np, link_d2):
@@ -69,27 +79,28 @@ def _check_group(r, g_members):
 
 
 def test_3d_groups_sampled(run):
-    lab = run["label"]
-    order = np.argsort(lab, kind="stable")
-    sl = lab[order]
-    starts = np.flatnonzero(np.r_[True, sl[1:] != sl[:-1]])
-    ends = np.r_[starts[1:], len(sl)]
-    sizes = ends - starts
+    hs = run["hs"]
+    sizes = hs[:, 1]
     rng = np.random.default_rng(3)
-    groups = []
+    labels = []
     # halos of every size class up to ~60k members (the oracle FOF of a neighbourhood
     # costs about 10 us per particle), and the groups of 20 random particles
     for lo_s, hi_s, k in ((20, 160, 6), (160, 5000, 6), (5000, 60000, 3)):
         idx = np.flatnonzero((sizes >= lo_s) & (sizes < hi_s))
-        groups += list(rng.choice(idx, size=min(k, len(idx)), replace=False))
-    where = np.searchsorted(sl, lab[rng.choice(len(lab), 20, replace=False)])
-    groups += list(np.searchsorted(starts, where, side="right") - 1)
+        labels += [int(hs[h, 0]) for h in rng.choice(idx, size=min(k, len(idx)), replace=False)]
+    labels += [int(run["label"][i]) for i in rng.choice(len(run["label"]), 20, replace=False)]
     big = 0
-    for gi in sorted(set(int(x) for x in groups)):
-        g = order[starts[gi]:ends[gi]]
+    for lab in sorted(set(labels)):
+        g = _members(run, lab)
         _check_group(run, g)
         big = max(big, len(g))
     assert big >= 5000
+    # the halo table lists exactly the groups of >= 20 members, in label order
+    cnt = torch.bincount(run["lab_t"].to(torch.int64), minlength=run["lab_t"].shape[0])
+    big_labels = torch.nonzero(cnt >= 20).squeeze(1).cpu().numpy()
+    assert np.array_equal(big_labels, hs[:, 0].astype(np.int64))
+    assert np.array_equal(cnt[big_labels].cpu().numpy(), hs[:, 1].astype(np.int64))
+    del cnt
 
 
 def _sample_halos(r, rng, nmax):
@@ -102,13 +113,11 @@ def _sample_halos(r, rng, nmax):
 
 def test_substructure_stages_sampled(run):
     box = run["box"]
-    off, mem = oracle.halos(run["label"], 20)
-    assert len(off) - 1 == run["nhalo"]
     rng = np.random.default_rng(4)
     nflags = 0
     for h in _sample_halos(run, rng, 150000):
-        m = mem[off[h]:off[h + 1]]
         hs = run["hs"][h]
+        m = _members(run, hs[0])
         assert hs[0] == m[0] and hs[1] == len(m)
         up = oracle.unwrap(box.pos, m)
         # f_l, member by member
