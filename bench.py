@@ -49,6 +49,10 @@ WORKLOADS = {
     "m160": "160^3 box (4.1M particles), same generator and parameters: small profiling case",
     "c1024": "1024^3 clustered box (1.07 B particles), 1 Gpc/h, same generator and parameters "
              "as the 512^3 box",
+    "prelabelled": "batching form: 200,000 pre-labelled halos (NFW hosts with dN/dM ~ M^-1.9 on "
+          "[20, 4e6], power-law Plummer subhalos, 92.7M particles, no background); "
+          "substructure search only (f_l, background R, fit, 6D links; no 3D FOF), same "
+          "search parameters",
 }
 SAMPLE_BOX = "m64"
 SAMPLE_DESC = ("64^3 box (262,144 particles) drawn by the same generator with the same "
@@ -194,13 +198,19 @@ def run_ours(args):
     L.vr_launch_count.restype = ctypes.c_int64
 
     t0 = time.time()
-    box = synth.named(args.workload, replica=rank)  # each rank: its own seeded box
+    prelab = args.workload == "prelabelled"  # pre-labelled halos: the step has no 3D FOF
+    if prelab:
+        box, lab_np = synth.prelabelled_halos(200000, synth.SEED0 + 3 + 100000 * rank)
+    else:
+        box = synth.named(args.workload, replica=rank)  # each rank: its own seeded box
     log(f"rank {rank}: generated {box.n} particles in {time.time() - t0:.1f}s")
     P = Params.default()
     ctx = Context(local)
     pos = torch.from_numpy(box.pos).to(dev)
     vel = torch.from_numpy(box.vel).to(dev)
     lab = torch.empty(box.n, dtype=torch.int32, device=dev)
+    if prelab:
+        lab.copy_(torch.from_numpy(lab_np))
     from paper_1902_01010_gb300.vr import alloc_outputs
 
     out = alloc_outputs(box.n, P, dev)
@@ -208,7 +218,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
 
     def step():
-        ctx.fof3d(pos, box.link_d2, label=lab)
+        if not prelab:
+            ctx.fof3d(pos, box.link_d2, label=lab)
         ctx.find_substructure(pos, vel, lab, box.lx_sub, 1.0, P, batched=batched, out=out)
 
     for _ in range(args.warmup):
@@ -257,21 +268,27 @@ def run_ours(args):
     if args.e2e_steps > 0:
         hpos = torch.from_numpy(box.pos).pin_memory()
         hvel = torch.from_numpy(box.vel).pin_memory()
-        hl3 = torch.empty(box.n, dtype=torch.int32).pin_memory()
+        hl3 = torch.empty(box.n, dtype=torch.int32).pin_memory()  # 3D labels: out, or in (pre-labelled)
+        if prelab:
+            hl3.copy_(torch.from_numpy(lab_np))
         hl6 = torch.empty(box.n, dtype=torch.int32).pin_memory()
         torch.cuda.synchronize(dev)
         t1 = time.perf_counter()
         for _ in range(args.e2e_steps):
             pos.copy_(hpos, non_blocking=True)
             vel.copy_(hvel, non_blocking=True)
+            if prelab:
+                lab.copy_(hl3, non_blocking=True)
             step()
-            hl3.copy_(lab, non_blocking=True)
+            if not prelab:
+                hl3.copy_(lab, non_blocking=True)
             hl6.copy_(out["label6"], non_blocking=True)
             torch.cuda.synchronize(dev)
         dt = (time.perf_counter() - t1) / args.e2e_steps
         e2e = {"value": ws * box.n / dt, "unit": "particles/s",
-               "h2d_bytes_per_step": int(hpos.numel() * 4 + hvel.numel() * 4),
-               "d2h_bytes_per_step": int(hl3.numel() * 4 + hl6.numel() * 4)}
+               "h2d_bytes_per_step": int(hpos.numel() * 4 + hvel.numel() * 4
+                                         + (hl3.numel() * 4 if prelab else 0)),
+               "d2h_bytes_per_step": int(hl6.numel() * 4 + (0 if prelab else hl3.numel() * 4))}
 
     # ---- rows beyond the headline step, on the same box (timed separately, 3 calls each):
     #      field 6DFOF of the 3DFOF halos (Sec. 2.1), significance cleaning of the outlier
@@ -279,7 +296,7 @@ def run_ours(args):
     #      the merge threshold (Sec. 2.2), the core search (Sec. 2.3, Eq. coreloop) and the
     #      core search followed by core cleaning and growth (Sec. 2.3, Eqs. coresig, coredist)
     next_rows = None
-    if args.next_rows:
+    if args.next_rows and not prelab:
         lx = 0.2 * synth.mean_spacing(box.n)
         l6f = torch.empty(box.n, dtype=torch.int32, device=dev)
         halos_f = torch.empty((box.n // P.nmin + 1, 12), dtype=torch.float64, device=dev)
@@ -366,7 +383,8 @@ def run_ours(args):
     plain = None
     if batched and args.plain_steps > 0:
         def step_plain():
-            ctx.fof3d(pos, box.link_d2, label=lab)
+            if not prelab:
+                ctx.fof3d(pos, box.link_d2, label=lab)
             ctx.find_substructure(pos, vel, lab, box.lx_sub, 1.0, P, batched=0, out=out)
 
         # no separate warm-up: every kernel and buffer was already used by the batched steps

@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(NT) k_cells_build(
   __shared__ int s_count;
   __shared__ uint32_t s_scan[NT];
   __shared__ unsigned long long s_keys[kSmallNode];
-  __shared__ uint32_t s_offl, s_offr;
+  __shared__ uint32_t s_wl[NT / 32], s_wr[NT / 32];
   if (first + (int64_t)blockIdx.x >= last) return;
   const int64_t h = horder[first + blockIdx.x];  // largest halos first
   const uint32_t hb = hoff[h], he = hoff[h + 1];
@@ -359,15 +359,14 @@ __global__ void __launch_bounds__(NT) k_cells_build(
       for (uint32_t i = nb_ + t; i < ne_; i += NT) cl += coord(u[perm[i]], a) < xs ? 1 : 0;
       const int nleft = block_reduce<NT>(cl, AddI(), s_ri);
       if (nleft == 0) continue;  // left side empty: next axis
-      // partition into tmp (left block, then right block; the order inside a block does
-      // not matter), warp-aggregated reservations on two shared counters
-      if (t == 0) {
-        s_offl = 0;
-        s_offr = 0;
-      }
-      __syncthreads();
+      // stable partition into tmp (left block, then right block, each in the node's
+      // order): per chunk, every warp's ballot counts are scanned across the warps, so
+      // the member order, and with it every later FP64 sum, does not depend on warp
+      // scheduling
       {
         const unsigned lt = (1u << (t & 31)) - 1u;
+        const int w = t >> 5, lane = t & 31;
+        uint32_t offl = 0, offr = 0;
         for (uint32_t cb = nb_; cb < ne_; cb += NT) {
           const uint32_t i = cb + t;
           const bool ok = i < ne_;
@@ -379,17 +378,30 @@ __global__ void __launch_bounds__(NT) k_cells_build(
           }
           const unsigned bl = __ballot_sync(0xffffffffu, ok && isl);
           const unsigned br = __ballot_sync(0xffffffffu, ok && !isl);
-          uint32_t basel = 0, baser = 0;
-          if ((t & 31) == 0) {
-            basel = atomicAdd(&s_offl, (uint32_t)__popc(bl));
-            baser = atomicAdd(&s_offr, (uint32_t)__popc(br));
+          if (lane == 0) {
+            s_wl[w] = (uint32_t)__popc(bl);
+            s_wr[w] = (uint32_t)__popc(br);
           }
-          basel = __shfl_sync(0xffffffffu, basel, 0);
-          baser = __shfl_sync(0xffffffffu, baser, 0);
+          __syncthreads();
+          // inclusive scan of the per-warp counts, redone by every warp
+          uint32_t xl = lane < NT / 32 ? s_wl[lane] : 0u, xr = lane < NT / 32 ? s_wr[lane] : 0u;
+          for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t yl = __shfl_up_sync(0xffffffffu, xl, o);
+            const uint32_t yr = __shfl_up_sync(0xffffffffu, xr, o);
+            if (lane >= o) {
+              xl += yl;
+              xr += yr;
+            }
+          }
+          const uint32_t basel = offl + __shfl_sync(0xffffffffu, xl, w) - (uint32_t)__popc(bl);
+          const uint32_t baser = offr + __shfl_sync(0xffffffffu, xr, w) - (uint32_t)__popc(br);
+          offl += __shfl_sync(0xffffffffu, xl, 31);
+          offr += __shfl_sync(0xffffffffu, xr, 31);
           if (ok) {
             if (isl) tmp[nb_ + basel + __popc(bl & lt)] = pm;
             else tmp[nb_ + nleft + baser + __popc(br & lt)] = pm;
           }
+          __syncthreads();  // s_wl / s_wr are rewritten by the next chunk
         }
       }
       __syncthreads();

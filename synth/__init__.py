@@ -51,6 +51,9 @@ def _load():
             ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
             ctypes.c_void_p, ctypes.c_void_p,
         ]
+        lib.synth_hosts_total.restype = ctypes.c_int64
+        lib.synth_hosts_total.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_double,
+                                          ctypes.c_double]
         _lib = lib
     return _lib
 
@@ -121,6 +124,31 @@ def mass_function_box(n: int, seed: int) -> Box:
     uniform background at 30 km/s."""
     return make_box(1, n, seed, frac_halo=0.4, size_lo=20, size_hi=1e6, conc_lo=4.0,
                     conc_hi=15.0, sigma_host=100.0, sigma_bg=30.0, name=f"massfn_{n}")
+
+
+def prelabelled_halos(nhost: int, seed: int, size_hi: float = 4e6):
+    """`nhost` pre-labelled halos and no background: NFW hosts with dN/dM ~ M^-1.9 on
+    [20, size_hi], c in [4, 15], sigma_host = 100 km/s (n_h/1000)^(1/3), power-law
+    Plummer subhalos, placed at random in the 2^21 lattice box (they may overlap: the
+    labels, not the positions, say which halo a particle belongs to). Returns (box,
+    label) with label = the minimum particle index of each particle's halo, the form of
+    the 3D FOF labels."""
+    n = int(_load().synth_hosts_total(seed, nhost, 20.0, size_hi))
+    lib = _load()
+    pos = np.empty((n, 3), np.int32)
+    vel = np.empty((n, 3), np.float32)
+    hid = np.empty(n, np.int32)
+    sid = np.empty(n, np.int32)
+    nh = lib.synth_box(n, 2, seed, nhost, 1.0, 20.0, size_hi, 4.0, 15.0, 100.0, 30.0,
+                       pos.ctypes.data, vel.ctypes.data, hid.ctypes.data, sid.ctypes.data)
+    if nh != nhost:
+        raise ValueError("synth_box rejected its arguments")
+    first = np.full(nhost, n, np.int64)
+    np.minimum.at(first, hid, np.arange(n, dtype=np.int64))
+    label = first[hid].astype(np.int32)
+    box = Box(f"prelabelled_{nhost}", n, pos, vel, hid, sid, nhost, link_d2_for(n),
+              0.1 * mean_spacing(n))
+    return box, label
 
 
 def named(name: str, replica: int = 0) -> Box:

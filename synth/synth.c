@@ -177,6 +177,14 @@ static void add_host(blist *l, uint64_t seed, int32_t hid, int64_t nh, double co
   }
 }
 
+/* Particles in kind 2's nhost hosts (the N to pass to synth_box). */
+int64_t synth_hosts_total(uint64_t seed, int nhost, double size_lo, double size_hi) {
+  int64_t tot = 0;
+  for (int h = 0; h < nhost; ++h)
+    tot += (int64_t)llround(powlaw(u01(seed, 78, (uint64_t)h), size_lo, size_hi, 1.9));
+  return tot;
+}
+
 static int64_t gcd64(int64_t a, int64_t b) {
   while (b) { int64_t t = a % b; a = b; b = t; }
   return a;
@@ -188,6 +196,9 @@ static int64_t gcd64(int64_t a, int64_t b) {
  * kind 1: hosts with sizes from dN/dM ~ M^-1.9 on [size_lo, size_hi] until frac_halo*N
  *         particles are in hosts; c uniform in [conc_lo, conc_hi];
  *         sigma_host = sigma_host0 (n_h/1000)^(1/3); power-law subhalos.
+ * kind 2: exactly nhost hosts drawn as in kind 1 but without the frac_halo cap, and no
+ *         background: N must be synth_hosts_total(seed, nhost, size_lo, size_hi)
+ *         (pre-labelled halos: host_id gives each particle's halo).
  * Writes pos[N][3] (int32 lattice), vel[N][3] (float km/s), and optional truth ids
  * host_id[N], sub_id[N] (-1 = none). Returns the number of hosts, or -1 on bad input.
  */
@@ -218,6 +229,16 @@ int64_t synth_box(int64_t N, int kind, uint64_t seed, int nhost, double frac_hal
       add_host(&l, seed, hid++, sizes[h], conc_lo, sigma_host0, nbar, 0, &nsub, sigma_bg);
       in_halo += sizes[h];
     }
+  } else if (kind == 2) {
+    for (int h = 0; h < nhost; ++h) {
+      int64_t nh = (int64_t)llround(powlaw(u01(seed, 78, (uint64_t)h), size_lo, size_hi, 1.9));
+      if (in_halo + nh > N) { free(l.b); return -1; }
+      double conc = conc_lo + (conc_hi - conc_lo) * u01(seed, 79, (uint64_t)h);
+      double sig = sigma_host0 * cbrt((double)nh / 1000.0);
+      add_host(&l, seed, hid++, nh, conc, sig, nbar, 1, &nsub, sigma_bg);
+      in_halo += nh;
+    }
+    if (in_halo != N) { free(l.b); return -1; }
   } else {
     int64_t target = (int64_t)llround(frac_halo * (double)N);
     for (uint64_t k = 0; in_halo < target; ++k) {
