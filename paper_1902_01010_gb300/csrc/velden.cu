@@ -19,7 +19,9 @@
 //  - h^2 is the largest kept |dv|^2, and the kernel sum runs over the kept list only
 //    (every neighbour with |dv| < h is in it).
 // Position keys are exact integers, so the N_se set equals the oracle's; velocity
-// differences and sums are FP32.
+// differences and sums are FP32. Squared separations are 64-bit integers, or 32-bit ones
+// wherever the two boxes involved (query bucket and candidate bucket or window) bound
+// every separation by 32767 lattice units per axis, which makes them exact in uint32.
 // Halos with at most N_se members use every member (one pass, no position search).
 #include <math.h>
 
@@ -33,8 +35,10 @@ namespace vr {
 namespace {
 
 constexpr int kNVMax = 64;
-constexpr int kBins = 64;
+constexpr int kBinBits = 6;      // histogram levels resolve kBinBits bits of the key
+constexpr int kBins = 1 << kBinBits;
 constexpr int kBuf = 32;
+constexpr int kBatch = 4;        // candidates whose distances are computed side by side
 constexpr int kWarps = 4;        // warps per block
 
 // Optional instrumentation (compile with -DVR_VELDEN_STATS): warp-level counts of the
@@ -123,6 +127,22 @@ __device__ __forceinline__ long long d2i(int4 a, int4 b) {
   long long dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
   return dx * dx + dy * dy + dz * dz;
 }
+// The same squared separation in 32-bit arithmetic, exact when every component of a - b
+// lies in [-32767, 32767]: then d^2 < 3 * 2^30 < 2^32.
+__device__ __forceinline__ uint32_t d2u(int4 a, int4 b) {
+  const int dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+  return (uint32_t)(dx * dx) + (uint32_t)(dy * dy) + (uint32_t)(dz * dz);
+}
+
+// True when every separation between a point of box A and a point of box B has all
+// components in [-32767, 32767] (d2u is then exact for every such pair).
+__device__ __forceinline__ bool fits32(int4 alo, int4 ahi, int4 blo, int4 bhi) {
+  const int ex = max(ahi.x - blo.x, bhi.x - alo.x), ey = max(ahi.y - blo.y, bhi.y - alo.y),
+            ez = max(ahi.z - blo.z, bhi.z - alo.z);
+  return max(ex, max(ey, ez)) <= 32767;
+}
+
+__device__ __forceinline__ uint32_t clamp32(u64 x) { return x > 0xffffffffull ? 0xffffffffu : (uint32_t)x; }
 
 // ---------------------------------------------------------------- small halos
 template <int NVM>
@@ -280,39 +300,81 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
     __syncwarp();
     VR_STAT(st, kStatPass0 + pass_id, 1);
   };
+  const int4 qlo = bmin[b], qhi = bmax[b];
   // 1. bound from the window of kWindow * N_se members around the bucket: the N_se-th
-  //    smallest distance among them, rounded up to a histogram bin edge
+  //    smallest distance among them, rounded up to a histogram bin edge. When the window's
+  //    box and the bucket's box bound every separation by 32767 per axis (a warp-uniform
+  //    test), the distances are exact in 32-bit arithmetic.
   long long r2 = 0;
   {
     const int W = (int)min((uint32_t)(kWindow * nse), nh);
     int64_t w0 = (int64_t)qs + 16 - W / 2;
     if (w0 + W > (int64_t)he) w0 = (int64_t)he - W;
     if (w0 < (int64_t)hs) w0 = hs;
+    int4 wlo = make_int4(0x7fffffff, 0x7fffffff, 0x7fffffff, 0);
+    int4 whi = make_int4(-0x7fffffff, -0x7fffffff, -0x7fffffff, 0);
+    for (int c = lane; c < W; c += 32) {
+      const int4 pw = u[w0 + c];
+      wlo.x = min(wlo.x, pw.x); wlo.y = min(wlo.y, pw.y); wlo.z = min(wlo.z, pw.z);
+      whi.x = max(whi.x, pw.x); whi.y = max(whi.y, pw.y); whi.z = max(whi.z, pw.z);
+    }
+    for (int o = 16; o; o >>= 1) {
+      wlo.x = min(wlo.x, __shfl_xor_sync(FULL, wlo.x, o));
+      wlo.y = min(wlo.y, __shfl_xor_sync(FULL, wlo.y, o));
+      wlo.z = min(wlo.z, __shfl_xor_sync(FULL, wlo.z, o));
+      whi.x = max(whi.x, __shfl_xor_sync(FULL, whi.x, o));
+      whi.y = max(whi.y, __shfl_xor_sync(FULL, whi.y, o));
+      whi.z = max(whi.z, __shfl_xor_sync(FULL, whi.z, o));
+    }
+    const bool wn = fits32(qlo, qhi, wlo, whi);  // warp-uniform
     long long wmax = 0;
+    uint32_t wmax32 = 0;
     for (int c = 0; c < W; c += 32) {
       const int cnt = min(32, W - c);
       stage((uint32_t)(w0 + c), cnt, false);
-      for (int t0 = 0; t0 < 32; t0 += 8) {
-        long long d[8];
+      if (wn) {
+        for (int t0 = 0; t0 < 32; t0 += kBatch) {
+          uint32_t d[kBatch];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) d[j] = d2i(q, sm.su[t0 + j]);
+          for (int j = 0; j < kBatch; ++j) d[j] = d2u(q, sm.su[t0 + j]);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) wmax = (t0 + j < cnt && d[j] > wmax) ? d[j] : wmax;
+          for (int j = 0; j < kBatch; ++j) wmax32 = (t0 + j < cnt && d[j] > wmax32) ? d[j] : wmax32;
+        }
+      } else {
+        for (int t0 = 0; t0 < 32; t0 += kBatch) {
+          long long d[kBatch];
+#pragma unroll
+          for (int j = 0; j < kBatch; ++j) d[j] = d2i(q, sm.su[t0 + j]);
+#pragma unroll
+          for (int j = 0; j < kBatch; ++j) wmax = (t0 + j < cnt && d[j] > wmax) ? d[j] : wmax;
+        }
       }
     }
+    if (wn) wmax = (long long)wmax32;
     for (int cb = 0; cb < kBins; ++cb) sm.hist[cb][lane] = 0;
-    int sh0 = bitlen64((unsigned long long)wmax) - 6;  // 64 bins over [0, 2^bitlen)
+    int sh0 = bitlen64((unsigned long long)wmax) - kBinBits;  // kBins bins over [0, 2^bitlen)
     if (sh0 < 0) sh0 = 0;
     for (int c = 0; c < W; c += 32) {
       const int cnt = min(32, W - c);
       stage((uint32_t)(w0 + c), cnt, false);
-      for (int t0 = 0; t0 < 32; t0 += 8) {
-        long long d[8];
+      if (wn) {  // wmax < 2^32, so sh0 <= 26
+        for (int t0 = 0; t0 < 32; t0 += kBatch) {
+          uint32_t d[kBatch];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) d[j] = d2i(q, sm.su[t0 + j]);
+          for (int j = 0; j < kBatch; ++j) d[j] = d2u(q, sm.su[t0 + j]);
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-          if (t0 + j < cnt) sm.hist[(unsigned)(d[j] >> sh0)][lane]++;
+          for (int j = 0; j < kBatch; ++j)
+            if (t0 + j < cnt) sm.hist[d[j] >> sh0][lane]++;
+        }
+      } else {
+        for (int t0 = 0; t0 < 32; t0 += kBatch) {
+          long long d[kBatch];
+#pragma unroll
+          for (int j = 0; j < kBatch; ++j) d[j] = d2i(q, sm.su[t0 + j]);
+#pragma unroll
+          for (int j = 0; j < kBatch; ++j)
+            if (t0 + j < cnt) sm.hist[(unsigned)(d[j] >> sh0)][lane]++;
+        }
       }
     }
     int cum = 0, bs = kBins - 1;
@@ -333,7 +395,6 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
   // Candidate buckets are enumerated on the fly in every pass: super-bucket boxes, then
   // bucket boxes, against the query bucket's box grown by the largest per-lane bound;
   // f(bucket index) is called warp-uniformly for every bucket that passes.
-  const int4 qlo = bmin[b], qhi = bmax[b];
   const uint32_t sb0 = sboff[h], sb1 = sboff[h + 1];
   auto for_each_bucket = [&](long long rmax2, auto &&f) {
     for (uint32_t sbase = sb0; sbase < sb1; sbase += 32) {
@@ -358,7 +419,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
   //    spreads its bins over [r2/4, r2] only (the N_se-th key lies near the bound) and
   //    counts the keys below in one register; later levels split the chosen bin.
   u64 klo = (u64)(r2 >> 2) << 22;
-  int sh = bitlen64((((u64)(r2 + 1)) << 22) - klo - 1) - 6;
+  int sh = bitlen64((((u64)(r2 + 1)) << 22) - klo - 1) - kBinBits;
   if (sh < 0) sh = 0;
   int need = nse_eff;
   bool settled = !valid;
@@ -378,13 +439,36 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
       const uint32_t s0 = hs + 32u * (bb - 32u * sb0);
       const int cnt = (int)min(32u, he - s0);
       stage(s0, cnt, false);
-      if (want) {
-        for (int t0 = 0; t0 < 32; t0 += 8) {
-          long long d[8];
+      // 32-bit route: the boxes bound every separation by 32767 per axis and the bins
+      // are at least one unit of d^2 wide, so a key's bin depends on d^2 alone (klo is a
+      // multiple of 2^22): bin = (d^2 - (klo >> 22)) >> (sh - 22)
+      const bool narrow = fits32(qlo, qhi, bmin[bb], bmax[bb]);
+      if (want && narrow && sh >= 22 && (klo & 0x3fffffull) == 0) {
+        const uint32_t r32 = clamp32((u64)rcur), dlo = clamp32(klo >> 22);
+        const int shd = sh - 22;
+        for (int t0 = 0; t0 < 32; t0 += kBatch) {
+          uint32_t d[kBatch];
 #pragma unroll
-          for (int j = 0; j < 8; ++j) d[j] = d2i(q, sm.su[t0 + j]);
+          for (int j = 0; j < kBatch; ++j) d[j] = d2u(q, sm.su[t0 + j]);
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
+          for (int j = 0; j < kBatch; ++j) {
+            if (t0 + j < cnt && d[j] <= r32) {
+              if (d[j] >= dlo) {
+                const uint32_t rel = shd >= 32 ? 0u : (d[j] - dlo) >> shd;
+                if (rel < kBins) sm.hist[rel][lane]++;
+              } else if (focus) {
+                ++below;
+              }
+            }
+          }
+        }
+      } else if (want) {
+        for (int t0 = 0; t0 < 32; t0 += kBatch) {
+          long long d[kBatch];
+#pragma unroll
+          for (int j = 0; j < kBatch; ++j) d[j] = d2i(q, sm.su[t0 + j]);
+#pragma unroll
+          for (int j = 0; j < kBatch; ++j) {
             if (d[j] <= rcur) {
               u64 key = ((u64)d[j] << 22) | (u64)sm.su[t0 + j].w;
               if (key >= klo) {
@@ -403,7 +487,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
         // the N_se-th key lies below the focused range: bin [0, klo) next
         const u64 hi = klo;
         klo = 0;
-        sh = bitlen64(hi - 1) - 6;
+        sh = bitlen64(hi - 1) - kBinBits;
         if (sh < 0) sh = 0;
         const long long top_d = (long long)((hi - 1) >> 22);
         rcur = top_d < rcur ? top_d : rcur;
@@ -431,7 +515,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
           need -= cum;
           const long long top_d = (long long)((klo + ((u64)1 << sh) - 1) >> 22);
           rcur = top_d < rcur ? top_d : rcur;
-          sh = sh >= 6 ? sh - 6 : 0;
+          sh = sh >= kBinBits ? sh - kBinBits : 0;
         }
       }
     }
@@ -454,13 +538,36 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
     const uint32_t s0 = hs + 32u * (bb - 32u * sb0);
     const int cnt = (int)min(32u, he - s0);
     stage(s0, cnt, true);
-    if (want) {
-      for (int t0 = 0; t0 < 32; t0 += 8) {
-        long long d[8];
+    // 32-bit route as in the histogram passes: with both final-bin edges multiples of
+    // 2^22, key < edge iff d^2 < edge >> 22
+    const bool narrow = fits32(qlo, qhi, bmin[bb], bmax[bb]);
+    if (want && narrow && ((fin_lo | fin_hi) & 0x3fffffull) == 0) {
+      const uint32_t r32 = clamp32((u64)rcur), flo = clamp32(fin_lo >> 22),
+                     fhi = clamp32(fin_hi >> 22);
+      for (int t0 = 0; t0 < 32; t0 += kBatch) {
+        uint32_t d[kBatch];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) d[j] = d2i(q, sm.su[t0 + j]);
+        for (int j = 0; j < kBatch; ++j) d[j] = d2u(q, sm.su[t0 + j]);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < kBatch; ++j) {
+          if (t0 + j < cnt && d[j] <= r32) {
+            const int t = t0 + j;
+            if (d[j] < flo) {
+              top_insert(top, lane, tv, nv_eff, dv2f(sm.sv[t], vq));
+            } else if (d[j] < fhi && nbuf < kBuf) {
+              sm.bslot[nbuf][lane] = s0 + (uint32_t)t;
+              ++nbuf;
+            }
+          }
+        }
+      }
+    } else if (want) {
+      for (int t0 = 0; t0 < 32; t0 += kBatch) {
+        long long d[kBatch];
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) d[j] = d2i(q, sm.su[t0 + j]);
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) {
           if (d[j] <= rcur) {
             const int t = t0 + j;
             u64 key = ((u64)d[j] << 22) | (u64)sm.su[t].w;

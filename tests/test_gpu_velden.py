@@ -28,7 +28,7 @@ def _gpu_fl(ctx, pos, vel, label, **kw):
     P = Params.default(**kw)
     f = ctx.velden(torch.from_numpy(np.ascontiguousarray(pos)).cuda(),
                    torch.from_numpy(np.ascontiguousarray(vel)).cuda(),
-                   torch.from_numpy(np.ascontiguousarray(label, np.int32)).cuda(), P)
+                   torch.from_numpy(np.array(label, np.int32)).cuda(), P)
     ctx.sync()
     return f.cpu().numpy()
 
