@@ -145,10 +145,10 @@ def measured_peaks():
 # Epanechnikov sum over N_v (3 ops): 256*8 + 256*8 + 256 + 256 + 32*3 = 4,704 ALU ops.
 VELDEN_OPS_PER_QUERY = 256 * 8 + 256 * 8 + 256 + 256 + 32 * 3
 # DRAM bytes per query particle of k_velden_big from one ncu capture of the 160^3 box
-# (41.6 MB over 1,183,473 queries; profiles/k_velden_big_160cubed.md). The kernel's DRAM
+# (41.9 MB over 1,183,473 queries; profiles/k_velden_big_160cubed.md). The kernel's DRAM
 # traffic grows with the number of queries, so a full launch is this times its queries.
 # Set to None whenever the kernel changes and the capture has not been redone.
-VELDEN_DRAM_BYTES_PER_QUERY = 41.572352e6 / 1183473
+VELDEN_DRAM_BYTES_PER_QUERY = 41.942784e6 / 1183473
 SMS, LANES_PER_SM = 152, 128
 
 
