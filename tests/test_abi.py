@@ -34,3 +34,24 @@ def test_params_default_is_table1():
     assert (p.nse, p.nv, p.nmin) == (256, 32, 20)
     assert p.f_cell == 0.01 and p.ell_th == 2.5 and p.v_ratio == 2.0
     assert abs(p.theta_op - 0.1 * 3.141592653589793) < 1e-15
+
+
+def _golden():
+    out = {}
+    with open(os.path.join(ROOT, "tests", "golden", "table1_defaults.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()[:2]
+                out[k] = float(v)
+    return out
+
+
+def test_core_defaults_are_table1():
+    """vr_core_params_default and vr_core_grow_params_default give the core-search and
+    core-growth defaults the paper prints (Table 1; Table A1 for the growth mode)."""
+    g = _golden()
+    c = vr.CoreParams.default()
+    assert (c.alpha_x, c.alpha_v, c.n_loop, c.f_c, c.alpha_n) == (
+        g["alpha_xC"], g["alpha_vC"], g["n_loopC"], g["f_C"], g["alpha_NC"])
+    cg = vr.CoreGrowParams.default()
+    assert (cg.beta_c, cg.mode) == (g["beta_C"], g["core_growth_mode"])

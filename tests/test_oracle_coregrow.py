@@ -119,6 +119,38 @@ def _purity_recovery(out, truth):
     return np.array(pur), np.array(rec)
 
 
+def _paper_mixture():
+    """The paper's printed figures (tests/golden/core_growth_mixture.txt)."""
+    import os
+
+    out = {}
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "core_growth_mixture.txt")
+    with open(path) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                q, pop, sc, te = line.split()
+                out[(q, pop)] = (float(sc), float(te))
+    return out
+
+
+def test_defaults_match_the_paper():
+    import os
+
+    g = {}
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                           "table1_defaults.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()[:2]
+                g[k] = float(v)
+    d = oracle.CORE_DEFAULTS
+    assert (d["ax"], d["av"], d["n_loop"], d["f_c"], d["an"]) == (
+        g["alpha_xC"], g["alpha_vC"], g["n_loopC"], g["f_C"], g["alpha_NC"])
+    assert (oracle.CORE_GROW_DEFAULTS["beta_c"], oracle.CORE_GROW_DEFAULTS["mode"]) == (
+        g["beta_C"], g["core_growth_mode"])
+
+
 def test_gaussian_mixture_tensor_vs_scalar():
     """Sec. 2.3's comparison, rebuilt: seeds of 100 particles per population set the
     dispersions, every other particle is assigned in one step. The paper reports, for a
@@ -131,6 +163,10 @@ def test_gaussian_mixture_tensor_vs_scalar():
     the tensor distance raises the aspherical population's purity (~0.88 -> ~0.99) and
     the spherical population's recovery (~0.88 -> ~0.99), because it stops assigning the
     spherical population's particles off the thin axis to the aspherical core."""
+    paper = _paper_mixture()
+    # the two figures pinned here move up from scalar to tensor in the paper too
+    assert paper[("purity", "aspherical")][1] > paper[("purity", "aspherical")][0]
+    assert paper[("recovery", "spherical")][1] > paper[("recovery", "spherical")][0]
     for seed in range(4):
         rng = np.random.default_rng(100 + seed)
         p0, p1 = _mixture(rng, 20000, 0.03)
