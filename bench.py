@@ -446,7 +446,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "int64 distances, f32 f_l, f64 background/fit/links", "data": "synthetic",
+        "dtype": "int64 and exact u32 distances, f32 f_l, f64 background/fit/links", "data": "synthetic",
         "config": {"workload": WORKLOADS.get(args.workload, args.workload),
                    "n_particles": box.n, "halos": int(out["nhalo"]), "form": args.form,
                    "l2": "inputs 24 B/particle >> 129 MB L2; no flush between steps",
