@@ -55,3 +55,25 @@ def test_core_defaults_are_table1():
         g["alpha_xC"], g["alpha_vC"], g["n_loopC"], g["f_C"], g["alpha_NC"])
     cg = vr.CoreGrowParams.default()
     assert (cg.beta_c, cg.mode) == (g["beta_C"], g["core_growth_mode"])
+
+
+def test_no_fallback_without_the_library(monkeypatch, tmp_path):
+    """With libvr.so missing (and no build), the binding raises instead of computing
+    anything on the host."""
+    import pytest
+
+    monkeypatch.setattr(vr, "_lib", None)
+    monkeypatch.setattr(_build, "LIB", str(tmp_path / "libvr.so"))
+    with pytest.raises(RuntimeError):
+        vr.lib(build_if_missing=False)
+
+
+def test_context_needs_a_gpu():
+    """Without a usable CUDA device, creating a context fails with a library status."""
+    import pytest
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(vr.VrError):
+        vr.Context(0)
