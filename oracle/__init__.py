@@ -78,7 +78,10 @@ def _lib_():
             "or_knn_one": (i64, [vp, vp, i64, i64, ctypes.c_int, vp]),
             "or_ncell": (i64, [i64, dbl, i32]),
             "or_ln_fbg": (dbl, [vp, vp, vp]),
-            "or_background_halo": (i64, [vp, vp, vp, i64, vp, dbl, i32, ctypes.c_int, vp, vp, vp]),
+            "or_background_halo": (i64, [vp, vp, vp, i64, vp, dbl, i32, ctypes.c_int, vp, vp, vp,
+                                          vp]),
+            "or_ell_bins": (ctypes.c_int, [vp, i64, ctypes.c_int, ctypes.c_int, vp, vp]),
+            "or_sg_fit": (None, [vp, i64, dbl, dbl, dbl, ctypes.c_int, vp]),
             "or_ell_fit": (ctypes.c_int, [vp, i64, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp]),
             "or_fof6d_halo": (ctypes.c_int, [vp, vp, vp, i64, vp, vp, dbl, dbl, ctypes.c_int,
                                              ctypes.c_int, i32, vp]),
@@ -185,8 +188,10 @@ def ln_fbg(v, vbar, sig6) -> float:
     return _lib_().or_ln_fbg(_p(v), _p(vbar), _p(sig6))
 
 
-def background_halo(upos, vel, members, f_l, f_cell=0.01, ncell_min=100, split_rule=0):
-    """Returns (R [nh], leaf_of [nh], cell_stats [nleaves, 13])."""
+def background_halo(upos, vel, members, f_l, f_cell=0.01, ncell_min=100, split_rule=0,
+                    boxes=False):
+    """Returns (R [nh], leaf_of [nh], cell_stats [nleaves, 13]), plus the leaves'
+    half-open regions [nleaves, 6] (lo[3], hi[3]) when boxes is set."""
     upos = _c(upos, np.int64)
     vel = _c(vel, np.float32)
     members = _c(members, np.int32)
@@ -195,11 +200,34 @@ def background_halo(upos, vel, members, f_l, f_cell=0.01, ncell_min=100, split_r
     R = np.empty(nh, np.float64)
     leaf = np.empty(nh, np.int32)
     cs = np.empty((max(nh, 1), 13), np.float64)
+    lb = np.empty((max(nh, 1), 6), np.int64) if boxes else None
     nl = _lib_().or_background_halo(_p(upos), _p(vel), _p(members), nh, _p(f_l), f_cell,
-                                    ncell_min, split_rule, _p(R), _p(leaf), _p(cs))
+                                    ncell_min, split_rule, _p(R), _p(leaf), _p(cs), _p(lb))
     if nl < 0:
         raise RuntimeError("oracle background failed")
+    if boxes:
+        return R, leaf, cs[:nl].copy(), lb[:nl].copy()
     return R, leaf, cs[:nl].copy()
+
+
+def ell_bins(R, nbins_min=10, nbins_max=200):
+    """(counts [nbins], (median, MAD', lo, width, nbins)); counts is empty when the
+    values are degenerate."""
+    R = _c(R, np.float64)
+    cnt = np.zeros(max(nbins_max, 1), np.float64)
+    meta = np.empty(5, np.float64)
+    _lib_().or_ell_bins(_p(R), R.shape[0], nbins_min, nbins_max, _p(cnt), _p(meta))
+    return cnt[: int(meta[4])].copy(), meta
+
+
+def sg_fit(counts, lo: float, width: float, sigma0: float, iters=100) -> np.ndarray:
+    """Fit of A f_SG to binned counts (bin b centred at lo + (b + 1/2) width):
+    (Rbar, sigma_R, s, A)."""
+    counts = _c(counts, np.float64)
+    out = np.empty(4, np.float64)
+    _lib_().or_sg_fit(_p(counts), counts.shape[0], float(lo), float(width), float(sigma0),
+                      iters, _p(out))
+    return out
 
 
 def ell_fit(R, nbins_min=10, nbins_max=200, iters=100) -> np.ndarray:

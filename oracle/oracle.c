@@ -549,10 +549,13 @@ double or_ln_fbg(const double *v, const double *vbar, const double *sig) {
  *  - R = ln f_l - ln f_bg (Eq. fvbg), NaN when the interpolated tensor is not PD.
  * f_l [nh] in member order; outputs R [nh], leaf_of [nh] (may be NULL),
  * cell_stats [nleaves][13] (mass, xbar[3], vbar[3], sig[6]; may be NULL, sized by the
- * caller to at least nh entries). Returns the number of leaves, or -1. */
+ * caller to at least nh entries), leaf_box [nleaves][6] (the half-open region lo[3],
+ * hi[3] of each leaf; may be NULL, sized like cell_stats). Returns the number of leaves,
+ * or -1. */
 int64_t or_background_halo(const int64_t *upos, const float *vel, const int32_t *members,
                            int64_t nh, const double *f_l, double f_cell, int32_t ncell_min,
-                           int split_rule, double *R, int32_t *leaf_of, double *cell_stats) {
+                           int split_rule, double *R, int32_t *leaf_of, double *cell_stats,
+                           int64_t *leaf_box) {
   if (nh <= 0) return 0;
   or_tree t;
   memset(&t, 0, sizeof(t));
@@ -663,6 +666,12 @@ int64_t or_background_halo(const int64_t *upos, const float *vel, const int32_t 
     if (leaf_of) leaf_of[m] = (int32_t)own;
   }
   if (cell_stats) memcpy(cell_stats, cs, (size_t)nl * 13 * sizeof(double));
+  if (leaf_box)
+    for (int64_t l = 0; l < nl; ++l)
+      for (int a = 0; a < 3; ++a) {
+        leaf_box[6 * l + a] = t.nodes[leaf_node[l]].lo[a];
+        leaf_box[6 * l + 3 + a] = t.nodes[leaf_node[l]].hi[a];
+      }
   free(cs);
   free(leaf);
   free(leaf_node);
@@ -737,24 +746,22 @@ static int or_solve4(double M[4][4], double *b, double *x) {
   return 1;
 }
 
-/* Fit of Eq. skewgaus to the binned R distribution of one halo (Sec. 2.2):
+/* Binning of one halo's R values for the fit of Eq. skewgaus (Sec. 2.2):
  *  - finite R values only; median and MAD' = 1.4826 * median |R - median|;
  *  - nbins = clamp(ceil(sqrt(N)), nbins_min, nbins_max) equal bins on
  *    [median - 6 MAD', median + 6 MAD'], bin = floor((R - lo) / width), values outside
- *    dropped;
- *  - Levenberg-Marquardt on the counts (unweighted least squares), start A = max count,
- *    Rbar = centre of the first fullest bin, sigma = MAD', s = 1; lambda = 1e-3, divided by
- *    10 on an accepted step and multiplied by 10 on a rejected one; at most `iters`
- *    iterations, stopping early when an accepted step changes the cost by less than
- *    1e-15 relative.
- * out = (Rbar, sigma_R, s, A, lo, width, nbins, MAD'). Returns 0, or 1 when degenerate
- * (fewer than 2 finite values or MAD' = 0: out[0] = median, out[1] = NaN). */
-int or_ell_fit(const double *R, int64_t nh, int nbins_min, int nbins_max, int iters, double *out) {
+ *    dropped.
+ * counts [nbins_max] out (may be NULL); meta = (median, MAD', lo, width, nbins) out.
+ * Returns 0, or 1 when degenerate (fewer than 2 finite values or MAD' = 0; meta[0] is
+ * the median when there are at least 2 values, NaN otherwise, and nbins is 0). */
+int or_ell_bins(const double *R, int64_t nh, int nbins_min, int nbins_max, double *counts,
+                double *meta) {
   double *a = (double *)malloc((size_t)(nh ? nh : 1) * sizeof(double));
   int64_t n = 0;
   for (int64_t i = 0; i < nh; ++i)
     if (isfinite(R[i])) a[n++] = R[i];
-  for (int k = 0; k < 8; ++k) out[k] = NAN;
+  for (int k = 0; k < 5; ++k) meta[k] = NAN;
+  meta[4] = 0.0;
   if (n < 2) { free(a); return 1; }
   qsort(a, (size_t)n, sizeof(double), or_cmp_double);
   double med = or_median_sorted(a, n);
@@ -763,8 +770,8 @@ int or_ell_fit(const double *R, int64_t nh, int nbins_min, int nbins_max, int it
   qsort(dev, (size_t)n, sizeof(double), or_cmp_double);
   double mad = 1.4826 * or_median_sorted(dev, n);
   free(dev);
-  out[0] = med;
-  out[7] = mad;
+  meta[0] = med;
+  meta[1] = mad;
   if (!(mad > 0.0)) { free(a); return 1; }
   int64_t nb = 0;
   while (nb * nb < n) ++nb; /* ceil(sqrt(n)) */
@@ -777,10 +784,26 @@ int or_ell_fit(const double *R, int64_t nh, int nbins_min, int nbins_max, int it
     if (f >= 0.0 && f < (double)nb) cnt[(int64_t)f] += 1.0;
   }
   free(a);
+  meta[2] = lo;
+  meta[3] = width;
+  meta[4] = (double)nb;
+  if (counts) memcpy(counts, cnt, (size_t)nb * sizeof(double));
+  free(cnt);
+  return 0;
+}
+
+/* Least-squares fit of Eq. skewgaus, A f_SG(x; Rbar, sigma, s), to nb binned counts
+ * whose bin b is centred at x_b = lo + (b + 1/2) width (Sec. 2.2): Levenberg-Marquardt,
+ * unweighted, started from A = max count, Rbar = centre of the first fullest bin,
+ * sigma = sigma0, s = 1; lambda = 1e-3, divided by 10 on an accepted step and multiplied
+ * by 10 on a rejected one; at most `iters` iterations, stopping early when an accepted
+ * step changes the cost by less than 1e-15 relative. out = (Rbar, sigma_R, s, A). */
+void or_sg_fit(const double *cnt, int64_t nb, double lo, double width, double sigma0,
+               int iters, double *out) {
   int64_t mode = 0;
   for (int64_t b = 1; b < nb; ++b)
     if (cnt[b] > cnt[mode]) mode = b;
-  double p[4] = {cnt[mode], lo + ((double)mode + 0.5) * width, mad, 1.0};
+  double p[4] = {cnt[mode], lo + ((double)mode + 0.5) * width, sigma0, 1.0};
   double lambda = 1e-3;
   double cost = 0.0;
   for (int64_t b = 0; b < nb; ++b) {
@@ -824,14 +847,34 @@ int or_ell_fit(const double *R, int64_t nh, int nbins_min, int nbins_max, int it
       if (lambda > 1e30) break;
     }
   }
-  free(cnt);
   out[0] = p[1];
   out[1] = p[2];
   out[2] = p[3];
   out[3] = p[0];
-  out[4] = lo;
-  out[5] = width;
-  out[6] = (double)nb;
+}
+
+/* Fit of Eq. skewgaus to the binned R distribution of one halo (Sec. 2.2): the binning
+ * of or_ell_bins, then or_sg_fit started from sigma = MAD'.
+ * out = (Rbar, sigma_R, s, A, lo, width, nbins, MAD'). Returns 0, or 1 when degenerate
+ * (fewer than 2 finite values or MAD' = 0: out[0] = median, out[1] = NaN). */
+int or_ell_fit(const double *R, int64_t nh, int nbins_min, int nbins_max, int iters, double *out) {
+  for (int k = 0; k < 8; ++k) out[k] = NAN;
+  double meta[5];
+  double *cnt = (double *)calloc((size_t)(nbins_max > 0 ? nbins_max : 1), sizeof(double));
+  int deg = or_ell_bins(R, nh, nbins_min, nbins_max, cnt, meta);
+  out[0] = meta[0];
+  out[7] = meta[1];
+  if (deg) { free(cnt); return 1; }
+  double fit[4];
+  or_sg_fit(cnt, (int64_t)meta[4], meta[2], meta[3], meta[1], iters, fit);
+  free(cnt);
+  out[0] = fit[0];
+  out[1] = fit[1];
+  out[2] = fit[2];
+  out[3] = fit[3];
+  out[4] = meta[2];
+  out[5] = meta[3];
+  out[6] = meta[4];
   return 0;
 }
 
@@ -1610,7 +1653,7 @@ int64_t or_pipeline(const int32_t *pos, const float *vel, int64_t n, int64_t lin
     }
     if (nh >= P->nsearch_min) {
       int64_t nl = or_background_halo(up, vel, m, nh, fl, P->f_cell, P->ncell_min,
-                                      P->split_rule, r, NULL, NULL);
+                                      P->split_rule, r, NULL, NULL, NULL);
       double fit[8];
       or_ell_fit(r, nh, P->fit_nbins_min, P->fit_nbins_max, P->fit_iters, fit);
       uint8_t *cand = (uint8_t *)malloc((size_t)nh);

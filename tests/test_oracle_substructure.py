@@ -240,6 +240,114 @@ def test_interpolation_two_cells():
         assert abs(R[k] - (math.log(f[k]) - lnfbg)) < 1e-10 * max(1, abs(R[k]))
 
 
+def _leaf_of_point(boxes, p):
+    """Index of the one leaf whose half-open region holds p, by a scan over every leaf."""
+    inside = np.all((boxes[:, :3] <= p) & (p < boxes[:, 3:]), axis=1)
+    hit = np.flatnonzero(inside)
+    assert len(hit) == 1, (p, hit)
+    return int(hit[0])
+
+
+def test_interpolation_multilevel_tree_brute_force():
+    """Face neighbours in a deep tree (Sec. 2.2, Eq. cellinterp), found without the tree:
+    for every member, the leaf holding its position moved to lo - 1 / hi of its own leaf
+    along each axis is found by scanning every leaf's half-open region; points outside
+    the root region are skipped and a leaf reached through two faces is counted once.
+    The moments are recomputed by numpy from the leaf membership, the interpolation and
+    ln f_bg (Eq. fvbg) by numpy's solve and determinant, and R must match to 1e-12."""
+    rng = np.random.default_rng(77)
+    nh = 12800  # N_cell = 128: seven levels of median splits, 128 leaves
+    # distinct coordinates on every axis, a dense clump plus a wider halo, anisotropic
+    core = rng.normal(0, [3000, 9000, 5000], size=(nh // 2, 3))
+    outer = rng.normal(0, [30000, 12000, 20000], size=(nh - nh // 2, 3))
+    p = np.concatenate([core, outer]) + 200000
+    upos = np.empty((nh, 3), np.int64)
+    for a in range(3):  # make each axis's coordinates distinct, keeping their order
+        order = np.argsort(p[:, a], kind="stable")
+        x = np.round(p[order, a]).astype(np.int64)
+        x = x + np.arange(nh)  # strictly increasing in sorted order
+        upos[order, a] = x
+    vel = rng.normal(0, 60, size=(nh, 3)).astype(np.float32)
+    vel[upos[:, 1] > np.median(upos[:, 1])] += np.float32([40, -10, 5])
+    members = np.arange(nh, dtype=np.int32)
+    f = np.exp(rng.normal(-14, 0.4, nh))
+    R, leaf, cs, boxes = oracle.background_halo(upos, vel, members, f, boxes=True)
+    nl = cs.shape[0]
+    assert nl == 128 and np.all(np.bincount(leaf, minlength=nl) == 100)
+
+    # the leaf regions tile the root region [min, max + 1) exactly and hold their members
+    root_lo, root_hi = upos.min(0), upos.max(0) + 1
+    assert np.all(boxes[:, :3] >= root_lo) and np.all(boxes[:, 3:] <= root_hi)
+    vol = np.prod((boxes[:, 3:] - boxes[:, :3]).astype(np.float64), axis=1)
+    assert vol.sum() == np.prod((root_hi - root_lo).astype(np.float64))
+    for i in range(nl):
+        for j in range(i + 1, nl):
+            overlap = np.all(np.maximum(boxes[i, :3], boxes[j, :3])
+                             < np.minimum(boxes[i, 3:], boxes[j, 3:]))
+            assert not overlap
+    for m in range(nh):
+        assert _leaf_of_point(boxes, upos[m]) == leaf[m]
+
+    # moments per leaf (Eqs. meanpos, meanvel, meandispvel) by numpy
+    mom = np.zeros((nl, 13))
+    for l in range(nl):
+        sel = leaf == l
+        v = vel[sel].astype(np.float64)
+        C = np.cov(v.T, bias=True)
+        mom[l] = [sel.sum(), *upos[sel].mean(0), *v.mean(0),
+                  C[0, 0], C[1, 1], C[2, 2], C[0, 1], C[0, 2], C[1, 2]]
+    assert np.allclose(cs, mom, rtol=1e-11, atol=1e-9)
+
+    # a split made at the root: a plane that no leaf region straddles
+    root_planes = [(a, x) for a in range(3) for x in np.unique(boxes[:, a])
+                   if x > root_lo[a] and np.all((boxes[:, 3 + a] <= x) | (boxes[:, a] >= x))]
+    assert root_planes
+    n_far, n_cross_root, n_dup, nneigh = 0, 0, 0, []
+    for m in range(nh):
+        own = leaf[m]
+        cells = [own]
+        for a in range(3):
+            for side in (0, 1):
+                q = upos[m].copy()
+                q[a] = boxes[own, a] - 1 if side == 0 else boxes[own, 3 + a]
+                if np.any(q < root_lo) or np.any(q >= root_hi):
+                    continue
+                c = _leaf_of_point(boxes, q)
+                n_dup += c in cells
+                if c not in cells:
+                    cells.append(c)
+                    other = [b for b in range(3) if b != a]
+                    # not a mirror image of the own leaf: its region differs across the face,
+                    # so the split between them was made two or more levels up
+                    if np.any(boxes[c, other] != boxes[own, other]) or np.any(
+                            boxes[c, [3 + b for b in other]] != boxes[own, [3 + b for b in other]]):
+                        n_far += 1
+                    for (ra, rx) in root_planes:
+                        if (boxes[own, ra] >= rx) != (boxes[c, ra] >= rx):
+                            n_cross_root += 1
+        nneigh.append(len(cells))
+        X = upos[m].astype(np.float64)
+        r = np.array([np.linalg.norm(X - mom[c, 1:4]) for c in cells])
+        if np.any(r == 0.0):
+            use = [cells[int(np.flatnonzero(r == 0.0)[0])]]
+            w = np.ones(1)
+        else:
+            use, w = cells, 1.0 / r
+        w = w / w.sum()
+        vb = (w[:, None] * mom[use, 4:7]).sum(0)
+        s6 = (w[:, None] * mom[use, 7:13]).sum(0)
+        S = np.array([[s6[0], s6[3], s6[4]], [s6[3], s6[1], s6[5]], [s6[4], s6[5], s6[2]]])
+        d = vel[m].astype(np.float64) - vb
+        lnfbg = (-0.5 * d @ np.linalg.solve(S, d) - 1.5 * math.log(2 * math.pi)
+                 - 0.5 * math.log(np.linalg.det(S)))
+        expect = math.log(f[m]) - lnfbg
+        assert abs(R[m] - expect) <= 1e-12 * max(1.0, abs(expect)), (m, R[m], expect)
+    assert n_far > 1000 and n_cross_root > 100
+    # leaves are disjoint boxes, so distinct faces of one leaf never reach the same
+    # neighbour; some members have neighbours across four faces
+    assert n_dup == 0 and max(nneigh) >= 5 and np.mean(nneigh) > 3.5
+
+
 def test_R_near_zero_on_smooth_gaussian_halo():
     """A halo-free Gaussian velocity field: R = ln(f_l/f_bg) should scatter around 0."""
     nh = 12000
@@ -274,6 +382,51 @@ def test_skew_gaussian_fit_recovers_planted():
     assert abs(fit[1] - sg) / sg < 0.03
     assert abs(fit[2] - s) / s < 0.05
     assert fit[6] == 200  # nbins clamp
+
+
+def _f_sg(x, A, mu, sg, s):
+    """Eq. skewgaus: width s*sigma left of the mode, sigma right of it."""
+    w = np.where(x < mu, s * sg, sg)
+    return A * np.exp(-((x - mu) ** 2) / (2 * w * w))
+
+
+@pytest.mark.parametrize("A,mu,sg,s", [(500.0, 0.3, 0.5, 1.6), (4321.0, -1.2, 0.8, 0.7),
+                                       (37.5, 2.0, 0.25, 1.0)])
+def test_sg_fit_exact_counts(A, mu, sg, s):
+    """Noise-free counts A f_SG at the bin centres x_b = lo + (b + 1/2) width of the
+    documented binning: the fit must return (Rbar, sigma_R, s, A) to 1e-8 relative. A bin
+    centre taken at the edge, or any offset in it, moves Rbar by up to half a bin."""
+    nb = 60
+    lo, width = mu - 6 * sg * max(s, 1.0), 12 * sg * max(s, 1.0) / nb
+    x = lo + (np.arange(nb) + 0.5) * width
+    counts = _f_sg(x, A, mu, sg, s)
+    fit = oracle.sg_fit(counts, lo, width, sigma0=1.3 * sg)
+    for got, want in zip(fit, (mu, sg, s, A)):
+        assert abs(got - want) <= 1e-8 * max(1.0, abs(want)), (fit, (mu, sg, s, A))
+
+
+def test_ell_bins_documented_binning():
+    """The binning step of the fit, recomputed by numpy: finite values only, median,
+    MAD' = 1.4826 median |R - median|, clamp(ceil(sqrt N), 10, 200) bins on
+    median -/+ 6 MAD', bin = floor((R - lo) / width)."""
+    rng = np.random.default_rng(12)
+    for n in (7, 99, 2500, 60000):
+        R = np.concatenate([rng.standard_t(5, n) * 0.7 + 0.2, [np.nan, np.inf, -np.inf]])
+        counts, meta = oracle.ell_bins(R)
+        a = R[np.isfinite(R)]
+        med = np.median(a)
+        mad = 1.4826 * np.median(np.abs(a - med))
+        nb = int(min(max(math.ceil(math.sqrt(len(a))), 10), 200))
+        lo, width = med - 6 * mad, 12 * mad / nb
+        assert meta[0] == med and meta[1] == mad and meta[4] == nb
+        assert meta[2] == lo and meta[3] == width
+        f = np.floor((a - lo) / width)
+        f = f[(f >= 0) & (f < nb)].astype(np.int64)
+        assert np.array_equal(counts, np.bincount(f, minlength=nb).astype(np.float64))
+        # the fit is this binning followed by the count fit started at sigma = MAD'
+        fit = oracle.ell_fit(R)
+        assert np.array_equal(fit[:4], oracle.sg_fit(counts, lo, width, mad))
+        assert fit[4] == lo and fit[5] == width and fit[6] == nb and fit[7] == mad
 
 
 def test_fit_degenerate():
