@@ -126,6 +126,20 @@ __global__ void k_unwrap(const int32_t *__restrict__ pos, const uint32_t *__rest
   }
 }
 
+// Every member is unwrapped to within 2^20 of the halo's first member, which gives one
+// consistent periodic image only when the halo spans less than half the box along each
+// axis; an unwrapped extent of 2^20 or more means it does not (error site 1).
+__global__ void k_halo_span(const int *__restrict__ bmin, const int *__restrict__ bmax, int64_t H,
+                            DevStatus *st) {
+  const int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= H) return;
+  for (int a = 0; a < 3; ++a)
+    if ((long long)bmax[3 * h + a] - bmin[3 * h + a] >= kHalf) {
+      raise_error(st, VR_ERR_UNSUPPORTED, 1);
+      return;
+    }
+}
+
 // key = halo id << 30 | 30-bit Morton code of the position scaled into the halo's
 // bounding cube (10 bits per axis); value = slot in (halo, index) order.
 __global__ void k_morton_keys(const int4 *__restrict__ u, const uint32_t *__restrict__ hkey,
@@ -290,6 +304,8 @@ vr_status build_halos(vr_ctx *ctx, const int32_t *pos, const float *vel, int64_t
   VR_CUDA(ctx, cudaMemsetAsync(B.bmax, 0x80, 3 * H * sizeof(int), s));
   k_unwrap<<<grid_for(NHP, T), T, 0, s>>>(pos, hkey, idx, g.hoff, g.hlabel, NHP, B.u_idx, B.bmin, B.bmax);
   VR_LAUNCHED(ctx, "k_unwrap");
+  k_halo_span<<<grid_for(H, T), T, 0, s>>>(B.bmin, B.bmax, H, ctx->d_status);
+  VR_LAUNCHED(ctx, "k_halo_span");
   k_morton_keys<<<grid_for(NHP, T), T, 0, s>>>(B.u_idx, hkey, B.bmin, B.bmax, NHP, B.mk0, B.mv0);
   VR_LAUNCHED(ctx, "k_morton_keys");
   VR_CUDA(ctx, radix_sort_pairs<u64>(B.mk0, B.mv0, B.mk1, B.mv1, NHP, 0, 30 + bitlen(H), B.scr, s,

@@ -26,6 +26,15 @@ size_t ws_substructure(int64_t n, const vr_params *p) {
 
 namespace {
 
+// A workspace below the documented size is refused before any launch.
+vr_status ws_upfront(vr_ctx *ctx, int64_t n, const vr_params *p, size_t ws_bytes) {
+  const size_t need = ws_substructure(n, p);
+  if (ws_bytes < need)
+    return set_error(ctx, VR_ERR_WORKSPACE_TOO_SMALL, "workspace too small: need %zu bytes, got %zu",
+                     need, ws_bytes);
+  return VR_OK;
+}
+
 vr_status common_checks(vr_ctx *ctx, int64_t n, const vr_params *p) {
   if (n < 0 || n >= (1LL << 31)) return set_error(ctx, VR_ERR_INVALID_ARG, "n must be in [0, 2^31)");
   return params_check(ctx, p);
@@ -60,6 +69,7 @@ vr_status vr_velden(vr_ctx *ctx, const int32_t *pos, const float *vel, int64_t n
   if (!pos || !vel || !label || !f_l || !ws) return set_error(ctx, VR_ERR_INVALID_ARG, "NULL pointer");
   cudaStream_t s = (cudaStream_t)stream;
   Arena ar(ws, ws_bytes);
+  if ((st = ws_upfront(ctx, n, p, ws_bytes)) != VR_OK) return st;
   HaloSeg g;
   st = fill_f32(ctx, f_l, n, NAN, s);
   if (st != VR_OK) return st;
@@ -81,6 +91,7 @@ vr_status vr_outlier_ratio(vr_ctx *ctx, const int32_t *pos, const float *vel, co
     return set_error(ctx, VR_ERR_INVALID_ARG, "NULL pointer");
   cudaStream_t s = (cudaStream_t)stream;
   Arena ar(ws, ws_bytes);
+  if ((st = ws_upfront(ctx, n, p, ws_bytes)) != VR_OK) return st;
   HaloSeg g;
   if ((st = fill_f32(ctx, R, n, NAN, s)) != VR_OK) return st;
   if ((st = fill_f32(ctx, ell, n, NAN, s)) != VR_OK) return st;
@@ -104,6 +115,7 @@ vr_status vr_fof6d(vr_ctx *ctx, const int32_t *pos, const float *vel, const floa
     return set_error(ctx, VR_ERR_INVALID_ARG, "NULL pointer");
   cudaStream_t s = (cudaStream_t)stream;
   Arena ar(ws, ws_bytes);
+  if ((st = ws_upfront(ctx, n, p, ws_bytes)) != VR_OK) return st;
   HaloSeg g;
   if ((st = fill_i32(ctx, label6, n, -1, s)) != VR_OK) return st;
   if ((st = build_halos(ctx, pos, vel, n, label, p->nmin, p->nse, ar, s, &g)) != VR_OK) return st;
@@ -128,6 +140,7 @@ vr_status vr_fof6d_field(vr_ctx *ctx, const int32_t *pos, const float *vel, int6
     return set_error(ctx, VR_ERR_INVALID_ARG, "lx and alpha_v must be positive");
   cudaStream_t s = (cudaStream_t)stream;
   Arena ar(ws, ws_bytes);
+  if ((st = ws_upfront(ctx, n, p, ws_bytes)) != VR_OK) return st;
   HaloSeg g;
   if ((st = fill_i32(ctx, label6, n, -1, s)) != VR_OK) return st;
   if ((st = build_halos(ctx, pos, vel, n, label, p->nmin, p->nse, ar, s, &g)) != VR_OK) return st;
@@ -167,6 +180,7 @@ vr_status vr_grow_groups(vr_ctx *ctx, const int32_t *pos, const float *vel, cons
     return set_error(ctx, VR_ERR_INVALID_ARG, "gamma_theta * theta_op must be < pi/2");
   cudaStream_t s = (cudaStream_t)stream;
   Arena ar(ws, ws_bytes);
+  if ((st = ws_upfront(ctx, n, p, ws_bytes)) != VR_OK) return st;
   HaloSeg g;
   if ((st = build_halos(ctx, pos, vel, n, label, p->nmin, p->nse, ar, s, &g)) != VR_OK) return st;
   if (nhalo != g.H)
@@ -203,6 +217,7 @@ vr_status vr_core_search(vr_ctx *ctx, const int32_t *pos, const float *vel, int6
     return set_error(ctx, VR_ERR_INVALID_ARG, "bad core search parameters");
   cudaStream_t s = (cudaStream_t)stream;
   Arena ar(ws, ws_bytes);
+  if ((st = ws_upfront(ctx, n, p, ws_bytes)) != VR_OK) return st;
   HaloSeg g;
   if ((st = build_halos(ctx, pos, vel, n, label, p->nmin, p->nse, ar, s, &g)) != VR_OK) return st;
   if ((st = run_halo_frame(ctx, g, p->nsearch_min, halo_stats, s)) != VR_OK) return st;
@@ -240,6 +255,7 @@ vr_status vr_core_grow(vr_ctx *ctx, const int32_t *pos, const float *vel, int64_
     return set_error(ctx, VR_ERR_INVALID_ARG, "bad core growth parameters");
   cudaStream_t s = (cudaStream_t)stream;
   Arena ar(ws, ws_bytes);
+  if ((st = ws_upfront(ctx, n, p, ws_bytes)) != VR_OK) return st;
   HaloSeg g;
   if ((st = build_halos(ctx, pos, vel, n, label, p->nmin, p->nse, ar, s, &g)) != VR_OK) return st;
   if ((st = run_halo_frame(ctx, g, p->nsearch_min, halo_stats, s)) != VR_OK) return st;
@@ -266,6 +282,7 @@ vr_status vr_clean_groups(vr_ctx *ctx, const float *ell, int64_t n, const vr_par
   if (!ell || !label6 || !ws) return set_error(ctx, VR_ERR_INVALID_ARG, "NULL pointer");
   if (!(beta >= 0.0)) return set_error(ctx, VR_ERR_INVALID_ARG, "beta must be >= 0");
   Arena ar(ws, ws_bytes);
+  if ((st = ws_upfront(ctx, n, p, ws_bytes)) != VR_OK) return st;
   return run_clean(ctx, ell, n, p, beta, label6, ngroups, ar, (cudaStream_t)stream);
 }
 
@@ -288,6 +305,7 @@ vr_status vr_find_substructure(vr_ctx *ctx, const int32_t *pos, const float *vel
   const bool plain = batched == 0;
   cudaStream_t s = (cudaStream_t)stream;
   Arena ar(ws, ws_bytes);
+  if ((st = ws_upfront(ctx, n, p, ws_bytes)) != VR_OK) return st;
   HaloSeg g;
   if ((st = fill_f32(ctx, f_l, n, NAN, s)) != VR_OK) return st;
   if ((st = fill_f32(ctx, R, n, NAN, s)) != VR_OK) return st;
