@@ -63,16 +63,17 @@ __device__ unsigned long long block_select(int n, int k, int nbits, Get get, uin
       if (hk == hp) atomicAdd(&s_dig[(key >> sh) & 0xffu], 1u);
     }
     __syncthreads();
-    uint32_t c = s_dig[t];
-    s_scan[t] = c;
-    __syncthreads();
-    for (int o = 1; o < 256; o <<= 1) {
-      uint32_t x = t >= o ? s_scan[t - o] : 0u;
-      __syncthreads();
-      s_scan[t] += x;
-      __syncthreads();
+    // inclusive scan of the 256 digit counts: warp scans, then the 8 warp totals
+    const uint32_t c = s_dig[t];
+    uint32_t incl = c;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t x = __shfl_up_sync(0xffffffffu, incl, o);
+      if ((t & 31) >= o) incl += x;
     }
-    uint32_t incl = s_scan[t], excl = incl - c;
+    if ((t & 31) == 31) s_scan[t >> 5] = incl;
+    __syncthreads();
+    for (int w = 0; w < (t >> 5); ++w) incl += s_scan[w];
+    const uint32_t excl = incl - c;
     const int rk = *s_rank;
     __syncthreads();
     if ((int)excl <= rk && rk < (int)incl) {

@@ -71,3 +71,24 @@ def test_noalloc_alternating_inputs_and_limits():
     big = torch.zeros((MAX_N + 1, 3), dtype=torch.int32, device="cuda")
     st, out = _call(f, big, 100)
     assert st == 1 and (out == -7).all()
+
+
+def test_noalloc_at_the_stated_maximum():
+    """n exactly VR_FOF3D_NOALLOC_MAX_N: the FOF scratch for that size fits the static array,
+    and the labels equal vr_fof3d's, twice in a row."""
+    from paper_1902_01010_gb300 import Context
+
+    f = _entry()
+    ctx = Context(0)
+    box = synth.mass_function_box(MAX_N, synth.SEED0 + 77)
+    assert box.n == MAX_N
+    pos = torch.from_numpy(box.pos).cuda()
+    ref = ctx.fof3d(pos, box.link_d2)
+    ctx.sync()
+    ref = ref.cpu().numpy()
+    assert len(np.unique(ref)) < MAX_N  # some groups formed
+    for call in range(2):
+        st, got = _call(f, pos, box.link_d2)
+        assert st == 0, (call, st)
+        assert np.array_equal(got, ref), call
+
