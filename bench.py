@@ -271,10 +271,15 @@ def run_ours(args):
             ctx.fof3d(pos, box.link_d2, label=lab)
         ctx.find_substructure(pos, vel, lab, box.lx_sub, 1.0, P, batched=batched, out=out)
 
+    # launch shapes: the first warm-up step times every candidate shape per halo-size bin
+    # on this machine and keeps the fastest (vr_autotune); the timed steps use the winners
+    if args.autotune:
+        ctx.autotune(True)
     for _ in range(args.warmup):
         step()
     ctx.sync()
     torch.cuda.synchronize(dev)
+    tuning = ctx.tuning_report()
 
     # ---- timed region: device-resident inputs
     if ws > 1:
@@ -532,6 +537,7 @@ def run_ours(args):
         "kernel_share_of_step": shares,
         "kernels": kernels,
         "plain_form": plain,
+        "tuning": tuning,
         "next_rows": next_rows,
         "parity": parity,
     }
@@ -826,6 +832,8 @@ def main():
     ap.add_argument("--no-next-rows", dest="next_rows", action="store_false",
                     help="skip timing field 6DFOF and group cleaning after the headline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="keep the default launch shapes instead of tuning them in the warm-up")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         log("note: warm-up raised to 3 steps")

@@ -355,8 +355,10 @@ vr_status vr_clean_groups(vr_ctx *ctx, const float *ell, int64_t n, const vr_par
  *   pos, n, link_d2, label: as for vr_fof3d, with n <= VR_FOF3D_NOALLOC_MAX_N
  *   stream: cudaStream_t on the current device (NULL = legacy default stream)
  * Works on the calling thread's current device. The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress); make that first call before any stream
- * capture. All calls share the one array and every call overwrites it: calls whose
+ * array's device address (cudaGetSymbolAddress) and keeps it for the process; make that
+ * first call before any stream capture. cudaDeviceReset on that device unloads the array
+ * with the library's module, so the kept address is then stale: do not call this entry
+ * point on a device again after resetting it in the same process. All calls share the one array and every call overwrites it: calls whose
  * work overlaps on the GPU (other streams, or host threads on the same device) race and
  * must be serialised by the caller. Returns VR_ERR_INVALID_ARG for n above the maximum
  * or bad arguments, VR_ERR_CUDA if the address lookup or a launch fails; the status code
@@ -385,6 +387,30 @@ vr_status vr_timing_reset(vr_ctx *ctx);
 /* Number of kernels this library has launched in the calling process so far (every
  * kernel, including those of the sort and scan primitives). */
 int64_t vr_launch_count(void);
+
+/* ---------------------------------------------------------------- autotuning
+ * (no counterpart in the paper: the launch shapes of this library's batched form)
+ * The f_l kernel runs one launch per halo-size bin (halos of more than 65536 members,
+ * 4097-65536, N_se+1-4096), each with its own shape (candidates computed side by side,
+ * register cap, warps per block); the 6D linker has one shape (32-candidate tiles per
+ * block). A shape changes how the same work is laid out on the GPU, never the arithmetic
+ * or its order: every shape gives bit-identical results.
+ * vr_autotune(ctx, 1): from the next call on, the first launch of each bin (and of the
+ * linker) with work runs every candidate shape on the caller's data, timed with CUDA
+ * events on `stream`, and keeps the fastest for later calls (that call takes several
+ * times longer and synchronises its stream). vr_autotune(ctx, 0) returns to the default
+ * shapes. Errors: VR_ERR_INVALID_ARG for enable not 0 or 1. */
+vr_status vr_autotune(vr_ctx *ctx, int enable);
+
+/* Every later launch uses f_l shape `velden_shape` and linker shape `link_shape` (indices
+ * into the candidate lists of vr_tuning_report; -1 = not forced). For testing that the
+ * shapes agree. Errors: VR_ERR_INVALID_ARG for an index out of range. */
+vr_status vr_tuning_force(vr_ctx *ctx, int velden_shape, int link_shape);
+
+/* Writes a JSON object with the candidate shapes, the shape in use per bin and the
+ * measured milliseconds (-1 where not measured) into buf (len bytes, NUL-terminated).
+ * Errors: VR_ERR_INVALID_ARG if buf is too small. */
+vr_status vr_tuning_report(const vr_ctx *ctx, char *buf, size_t len);
 
 #ifdef __cplusplus
 }

@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "stages.h"
+#include "tuning.cuh"
 #include "vr_workspace.h"
 #include "unionfind.cuh"
 
@@ -184,7 +185,7 @@ __device__ __forceinline__ void hash_add(const GrowArgs &G, u64 key) {
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(128) k_link6(const uint32_t *__restrict__ toff,
+__global__ void __launch_bounds__(256) k_link6(const uint32_t *__restrict__ toff,
                                                const uint32_t *__restrict__ coff,
                                                const uint32_t *__restrict__ thalo, int64_t t0,
                                                int64_t t1, const int4 *__restrict__ cu,
@@ -194,11 +195,11 @@ __global__ void __launch_bounds__(128) k_link6(const uint32_t *__restrict__ toff
                                                const double *__restrict__ hp, double vr2,
                                                double cos2, int use_lv, int use_vt, int *parent,
                                                GrowArgs G) {
-  __shared__ int4 s_u[4][32];
-  __shared__ float4 s_v[4][32];
-  __shared__ int s_r[4][32];
-  __shared__ int s_x[4][32];
-  __shared__ int s_y[4][32];
+  __shared__ int4 s_u[8][32];  // one row per warp (up to 8 warps per block)
+  __shared__ float4 s_v[8][32];
+  __shared__ int s_r[8][32];
+  __shared__ int s_x[8][32];
+  __shared__ int s_y[8][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const unsigned FULL = 0xffffffffu;
   const int64_t ti = t0 + (int64_t)blockIdx.x * (blockDim.x / 32) + w;  // tiles [t0, t1)
@@ -682,10 +683,43 @@ vr_status run_fof6d(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Arena &ar
       VR_LAUNCHED(ctx, "k_link6");
     }
   } else {
-    VR_TIMED(ctx, "link6", s, k_link6<kLink><<<grid_for(C.ntiles, 4), 128, 0, s>>>(
-        C.toff, C.coff, C.thalo, 0, C.ntiles, C.cu, C.cv, C.tmin, C.tmax, hp, vr2, cos2,
-        p->use_lv, p->use_vr_theta, C.parent, G));
-    VR_LAUNCHED(ctx, "k_link6");
+    // tiles per block from the tuning state; a linker still to be tuned is run once per
+    // candidate shape from fresh sets (same labels each time) and keeps the fastest
+    auto link = [&](int sh) {
+      const int w = kLWarps[sh];
+      k_link6<kLink><<<grid_for(C.ntiles, w), 32 * w, 0, s>>>(
+          C.toff, C.coff, C.thalo, 0, C.ntiles, C.cu, C.cv, C.tmin, C.tmax, hp, vr2, cos2,
+          p->use_lv, p->use_vr_theta, C.parent, G);
+    };
+    if (lmeasure(ctx)) {
+      Tuning *tn = ctx->tune;
+      cudaEvent_t e0, e1;
+      VR_CUDA(ctx, cudaEventCreate(&e0));
+      VR_CUDA(ctx, cudaEventCreate(&e1));
+      int best = 0;
+      for (int sh = 0; sh < kNLShapes; ++sh) {
+        if (sh > 0) {
+          k_cand_init<<<grid_for(C.nc, T), T, 0, s>>>(C.nc, C.parent, C.minidx, C.size);
+          VR_LAUNCHED(ctx, "k_cand_init");
+        }
+        VR_CUDA(ctx, cudaEventRecord(e0, s));
+        link(sh);
+        VR_LAUNCHED(ctx, "k_link6");
+        VR_CUDA(ctx, cudaEventRecord(e1, s));
+        VR_CUDA(ctx, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        VR_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
+        tn->lms[sh] = ms;
+        if (ms < tn->lms[best]) best = sh;
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      tn->lshape = best;
+      tn->ltuned = 1;
+    } else {
+      VR_TIMED(ctx, "link6", s, link(lshape_for(ctx)));
+      VR_LAUNCHED(ctx, "k_link6");
+    }
   }
   k_cand_roots<<<grid_for(C.nc, T), T, 0, s>>>(C.parent, C.cv, C.nc, C.minidx, C.size);
   VR_LAUNCHED(ctx, "k_cand_roots");

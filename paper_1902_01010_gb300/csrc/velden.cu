@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "halos.cuh"
+#include "tuning.cuh"
 #include "vr_workspace.h"
 
 namespace vr {
@@ -38,7 +39,6 @@ constexpr int kNVMax = 64;
 constexpr int kBinBits = 6;      // histogram levels resolve kBinBits bits of the key
 constexpr int kBins = 1 << kBinBits;
 constexpr int kBuf = 32;
-constexpr int kBatch = 4;        // candidates whose distances are computed side by side
 constexpr int kWarps = 4;        // warps per block
 
 // Optional instrumentation (compile with -DVR_VELDEN_STATS): warp-level counts of the
@@ -177,35 +177,63 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_small(
 }
 
 // ------------------------------------------------------------- bucket boxes
-// Buckets of halo h occupy the padded index range [32 sboff[h], 32 sboff[h+1]); bucket
-// b of the halo holds slots [hoff[h] + 32 b, min(hoff[h+1], hoff[h] + 32 b + 32)).
-__global__ void k_sb_count(const uint32_t *__restrict__ hoff, int64_t H, int nse,
-                           uint32_t *__restrict__ nsb) {
-  int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (h > H) return;
-  if (h == H) {
-    nsb[H] = 0;
+// Super-buckets are laid out halo by halo in the size order (largest first), so that the
+// buckets of each halo-size bin form one contiguous range. Halo h owns super-buckets
+// [sbs[h], sbe[h]); its bucket b (0-based) holds slots [hoff[h] + 32 b,
+// min(hoff[h+1], hoff[h] + 32 b + 32)) and has the global index 32 sbs[h] + b.
+__global__ void k_sb_count(const uint32_t *__restrict__ hoff, const uint32_t *__restrict__ horder,
+                           int64_t H, int nse, uint32_t *__restrict__ sbr) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r > H) return;
+  if (r == H) {
+    sbr[H] = 0;
     return;
   }
+  const uint32_t h = horder[r];
   uint32_t nh = hoff[h + 1] - hoff[h];
   uint32_t nb = (nh + 31) / 32;
-  nsb[h] = nh > (uint32_t)nse ? (nb + 31) / 32 : 0;
+  sbr[r] = nh > (uint32_t)nse ? (nb + 31) / 32 : 0;
 }
 
-__global__ void k_sb_fill(const uint32_t *__restrict__ sboff, int64_t H, uint32_t *__restrict__ sbhalo) {
-  int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (h >= H) return;
-  for (uint32_t s = sboff[h]; s < sboff[h + 1]; ++s) sbhalo[s] = (uint32_t)h;
+__global__ void k_sb_fill(const uint32_t *__restrict__ sbr, const uint32_t *__restrict__ horder,
+                          int64_t H, uint32_t *__restrict__ sbs, uint32_t *__restrict__ sbe,
+                          uint32_t *__restrict__ sbhalo) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= H) return;
+  const uint32_t h = horder[r];
+  sbs[h] = sbr[r];
+  sbe[h] = sbr[r + 1];
+  for (uint32_t s = sbr[r]; s < sbr[r + 1]; ++s) sbhalo[s] = h;
 }
 
-__global__ void k_bucket_boxes(const uint32_t *__restrict__ hoff, const uint32_t *__restrict__ sboff,
+// First super-bucket of the halos of at most kVBinEdge0 and at most kVBinEdge1 members
+// (sizes decrease along the order; the total when no halo is that small).
+__global__ void k_bin_edges(const uint32_t *__restrict__ hoff, const uint32_t *__restrict__ horder,
+                            const uint32_t *__restrict__ sbr, int64_t H, uint32_t *__restrict__ edges) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= H) return;
+  const uint32_t hr = horder[r];
+  const uint32_t nr = hoff[hr + 1] - hoff[hr];
+  uint32_t np = 0xffffffffu;
+  if (r > 0) {
+    const uint32_t hp = horder[r - 1];
+    np = hoff[hp + 1] - hoff[hp];
+  }
+  const uint32_t e[2] = {kVBinEdge0, kVBinEdge1};
+  for (int k = 0; k < 2; ++k) {
+    if (np > e[k] && nr <= e[k]) edges[k] = sbr[r];
+    if (r == H - 1 && nr > e[k]) edges[k] = sbr[H];
+  }
+}
+
+__global__ void k_bucket_boxes(const uint32_t *__restrict__ hoff, const uint32_t *__restrict__ sbs,
                                const uint32_t *__restrict__ sbhalo, int64_t nbpad,
                                const int4 *__restrict__ u, int4 *__restrict__ bmin,
                                int4 *__restrict__ bmax) {
   int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nbpad) return;
   uint32_t h = sbhalo[b >> 5];
-  uint32_t local = (uint32_t)b - 32u * sboff[h];
+  uint32_t local = (uint32_t)b - 32u * sbs[h];
   uint32_t s0 = hoff[h] + 32u * local, s1 = min(s0 + 32u, hoff[h + 1]);
   int4 lo = make_int4(0x7fffffff, 0x7fffffff, 0x7fffffff, 0);
   int4 hi = make_int4(-0x7fffffff, -0x7fffffff, -0x7fffffff, 0);
@@ -252,10 +280,13 @@ __device__ __forceinline__ long long pt_box_d2(int4 p, int4 blo, int4 bhi) {
 __device__ __forceinline__ int bitlen64(unsigned long long x) { return x ? 64 - __clzll(x) : 0; }
 
 // ---------------------------------------------------------------- big halos
-template <int NVM>
-__global__ void __launch_bounds__(32 * kWarps) k_velden_big(
-    const uint32_t *__restrict__ hoff, const uint32_t *__restrict__ sboff,
-    const uint32_t *__restrict__ sbhalo, int64_t b0, int64_t b1, const int4 *__restrict__ u,
+// Launch shape (tuning.cuh): BATCH candidates computed side by side, at most MAXREG
+// registers, any number of warps per block up to 8 (blockDim.x / 32).
+template <int NVM, int BATCH, int MAXREG>
+__global__ void __launch_bounds__(256) __maxnreg__(MAXREG) k_velden_big(
+    const uint32_t *__restrict__ hoff, const uint32_t *__restrict__ sbs,
+    const uint32_t *__restrict__ sbe, const uint32_t *__restrict__ sbhalo, int64_t b0,
+    int64_t b1, const int4 *__restrict__ u,
     const float4 *__restrict__ v, const int4 *__restrict__ bmin, const int4 *__restrict__ bmax,
     const int4 *__restrict__ smin, const int4 *__restrict__ smax, int nse, int nv,
     float *__restrict__ f_l, DevStatus *st) {
@@ -263,12 +294,13 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
   WarpSmem<NVM> &sm = reinterpret_cast<WarpSmem<NVM> *>(smem_raw)[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   const unsigned FULL = 0xffffffffu;
-  const int64_t b = b0 + (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);  // buckets [b0, b1)
+  const int64_t b = b0 + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);  // buckets [b0, b1)
   if (b >= b1) return;
   const uint32_t h = sbhalo[b >> 5];
   const uint32_t hs = hoff[h], he = hoff[h + 1];
   const uint32_t nh = he - hs;
-  const uint32_t local = (uint32_t)b - 32u * sboff[h];
+  const uint32_t sb0 = sbs[h], sb1 = sbe[h];
+  const uint32_t local = (uint32_t)b - 32u * sb0;
   const uint32_t nbh = (nh + 31) / 32;
   if (local >= nbh) return;  // padding bucket
   const uint32_t qs = hs + 32u * local, qe = min(qs + 32u, he);
@@ -333,20 +365,20 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
       const int cnt = min(32, W - c);
       stage((uint32_t)(w0 + c), cnt, false);
       if (wn) {
-        for (int t0 = 0; t0 < 32; t0 += kBatch) {
-          uint32_t d[kBatch];
+        for (int t0 = 0; t0 < 32; t0 += BATCH) {
+          uint32_t d[BATCH];
 #pragma unroll
-          for (int j = 0; j < kBatch; ++j) d[j] = d2u(q, sm.su[t0 + j]);
+          for (int j = 0; j < BATCH; ++j) d[j] = d2u(q, sm.su[t0 + j]);
 #pragma unroll
-          for (int j = 0; j < kBatch; ++j) wmax32 = (t0 + j < cnt && d[j] > wmax32) ? d[j] : wmax32;
+          for (int j = 0; j < BATCH; ++j) wmax32 = (t0 + j < cnt && d[j] > wmax32) ? d[j] : wmax32;
         }
       } else {
-        for (int t0 = 0; t0 < 32; t0 += kBatch) {
-          long long d[kBatch];
+        for (int t0 = 0; t0 < 32; t0 += BATCH) {
+          long long d[BATCH];
 #pragma unroll
-          for (int j = 0; j < kBatch; ++j) d[j] = d2i(q, sm.su[t0 + j]);
+          for (int j = 0; j < BATCH; ++j) d[j] = d2i(q, sm.su[t0 + j]);
 #pragma unroll
-          for (int j = 0; j < kBatch; ++j) wmax = (t0 + j < cnt && d[j] > wmax) ? d[j] : wmax;
+          for (int j = 0; j < BATCH; ++j) wmax = (t0 + j < cnt && d[j] > wmax) ? d[j] : wmax;
         }
       }
     }
@@ -358,21 +390,21 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
       const int cnt = min(32, W - c);
       stage((uint32_t)(w0 + c), cnt, false);
       if (wn) {  // wmax < 2^32, so sh0 <= 26
-        for (int t0 = 0; t0 < 32; t0 += kBatch) {
-          uint32_t d[kBatch];
+        for (int t0 = 0; t0 < 32; t0 += BATCH) {
+          uint32_t d[BATCH];
 #pragma unroll
-          for (int j = 0; j < kBatch; ++j) d[j] = d2u(q, sm.su[t0 + j]);
+          for (int j = 0; j < BATCH; ++j) d[j] = d2u(q, sm.su[t0 + j]);
 #pragma unroll
-          for (int j = 0; j < kBatch; ++j)
+          for (int j = 0; j < BATCH; ++j)
             if (t0 + j < cnt) sm.hist[d[j] >> sh0][lane]++;
         }
       } else {
-        for (int t0 = 0; t0 < 32; t0 += kBatch) {
-          long long d[kBatch];
+        for (int t0 = 0; t0 < 32; t0 += BATCH) {
+          long long d[BATCH];
 #pragma unroll
-          for (int j = 0; j < kBatch; ++j) d[j] = d2i(q, sm.su[t0 + j]);
+          for (int j = 0; j < BATCH; ++j) d[j] = d2i(q, sm.su[t0 + j]);
 #pragma unroll
-          for (int j = 0; j < kBatch; ++j)
+          for (int j = 0; j < BATCH; ++j)
             if (t0 + j < cnt) sm.hist[(unsigned)(d[j] >> sh0)][lane]++;
         }
       }
@@ -395,7 +427,6 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
   // Candidate buckets are enumerated on the fly in every pass: super-bucket boxes, then
   // bucket boxes, against the query bucket's box grown by the largest per-lane bound;
   // f(bucket index) is called warp-uniformly for every bucket that passes.
-  const uint32_t sb0 = sboff[h], sb1 = sboff[h + 1];
   auto for_each_bucket = [&](long long rmax2, auto &&f) {
     for (uint32_t sbase = sb0; sbase < sb1; sbase += 32) {
       uint32_t sx = sbase + lane;
@@ -446,12 +477,12 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
       if (want && narrow && sh >= 22 && (klo & 0x3fffffull) == 0) {
         const uint32_t r32 = clamp32((u64)rcur), dlo = clamp32(klo >> 22);
         const int shd = sh - 22;
-        for (int t0 = 0; t0 < 32; t0 += kBatch) {
-          uint32_t d[kBatch];
+        for (int t0 = 0; t0 < 32; t0 += BATCH) {
+          uint32_t d[BATCH];
 #pragma unroll
-          for (int j = 0; j < kBatch; ++j) d[j] = d2u(q, sm.su[t0 + j]);
+          for (int j = 0; j < BATCH; ++j) d[j] = d2u(q, sm.su[t0 + j]);
 #pragma unroll
-          for (int j = 0; j < kBatch; ++j) {
+          for (int j = 0; j < BATCH; ++j) {
             if (t0 + j < cnt && d[j] <= r32) {
               if (d[j] >= dlo) {
                 const uint32_t rel = shd >= 32 ? 0u : (d[j] - dlo) >> shd;
@@ -463,12 +494,12 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
           }
         }
       } else if (want) {
-        for (int t0 = 0; t0 < 32; t0 += kBatch) {
-          long long d[kBatch];
+        for (int t0 = 0; t0 < 32; t0 += BATCH) {
+          long long d[BATCH];
 #pragma unroll
-          for (int j = 0; j < kBatch; ++j) d[j] = d2i(q, sm.su[t0 + j]);
+          for (int j = 0; j < BATCH; ++j) d[j] = d2i(q, sm.su[t0 + j]);
 #pragma unroll
-          for (int j = 0; j < kBatch; ++j) {
+          for (int j = 0; j < BATCH; ++j) {
             if (d[j] <= rcur) {
               u64 key = ((u64)d[j] << 22) | (u64)sm.su[t0 + j].w;
               if (key >= klo) {
@@ -544,12 +575,12 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
     if (want && narrow && ((fin_lo | fin_hi) & 0x3fffffull) == 0) {
       const uint32_t r32 = clamp32((u64)rcur), flo = clamp32(fin_lo >> 22),
                      fhi = clamp32(fin_hi >> 22);
-      for (int t0 = 0; t0 < 32; t0 += kBatch) {
-        uint32_t d[kBatch];
+      for (int t0 = 0; t0 < 32; t0 += BATCH) {
+        uint32_t d[BATCH];
 #pragma unroll
-        for (int j = 0; j < kBatch; ++j) d[j] = d2u(q, sm.su[t0 + j]);
+        for (int j = 0; j < BATCH; ++j) d[j] = d2u(q, sm.su[t0 + j]);
 #pragma unroll
-        for (int j = 0; j < kBatch; ++j) {
+        for (int j = 0; j < BATCH; ++j) {
           if (t0 + j < cnt && d[j] <= r32) {
             const int t = t0 + j;
             if (d[j] < flo) {
@@ -562,12 +593,12 @@ __global__ void __launch_bounds__(32 * kWarps) k_velden_big(
         }
       }
     } else if (want) {
-      for (int t0 = 0; t0 < 32; t0 += kBatch) {
-        long long d[kBatch];
+      for (int t0 = 0; t0 < 32; t0 += BATCH) {
+        long long d[BATCH];
 #pragma unroll
-        for (int j = 0; j < kBatch; ++j) d[j] = d2i(q, sm.su[t0 + j]);
+        for (int j = 0; j < BATCH; ++j) d[j] = d2i(q, sm.su[t0 + j]);
 #pragma unroll
-        for (int j = 0; j < kBatch; ++j) {
+        for (int j = 0; j < BATCH; ++j) {
           if (d[j] <= rcur) {
             const int t = t0 + j;
             u64 key = ((u64)d[j] << 22) | (u64)sm.su[t].w;
@@ -614,7 +645,10 @@ size_t velden_bytes(int64_t n, int nmin) {
   Arena ar;
   int64_t hmax = n / (nmin > 0 ? nmin : 1) + 2;
   int64_t nbmax = n / 32 + 32 * hmax + 64;  // padded buckets
-  ar.take<uint32_t>(hmax + 1);  // nsb / sboff
+  ar.take<uint32_t>(hmax + 1);  // sbr
+  ar.take<uint32_t>(hmax);      // sbs
+  ar.take<uint32_t>(hmax);      // sbe
+  ar.take<uint32_t>(4);         // bin edges
   ar.take<uint32_t>(nbmax / 32 + 1);  // sbhalo
   ar.take<int4>(nbmax);   // bmin
   ar.take<int4>(nbmax);   // bmax
@@ -624,6 +658,22 @@ size_t velden_bytes(int64_t n, int nmin) {
   return ar.off;
 }
 
+namespace {
+
+// The f_l kernel instance for launch shape `shape` (tuning.cuh); N_v above 32 always uses
+// the default shape.
+template <int NVM>
+void *big_kernel(int shape) {
+  if (NVM > 32) return (void *)k_velden_big<NVM, 4, 80>;
+  switch (kVShapes[shape].batch) {
+    case 2: return (void *)k_velden_big<NVM, 2, 80>;
+    case 8: return (void *)k_velden_big<NVM, 8, 96>;
+    default: return (void *)k_velden_big<NVM, 4, 80>;
+  }
+}
+
+}  // namespace
+
 // Runs the f_l stage on an existing segmentation; f_l must already hold NaN outside
 // halos.
 vr_status run_velden(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Arena &ar, float *f_l,
@@ -632,7 +682,10 @@ vr_status run_velden(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Arena &a
   const int64_t H = g.H;
   int64_t hmax = g.n / (p->nmin > 0 ? p->nmin : 1) + 2;
   int64_t nbmax = g.n / 32 + 32 * hmax + 64;
-  uint32_t *sboff = ar.take<uint32_t>(hmax + 1);
+  uint32_t *sbr = ar.take<uint32_t>(hmax + 1);
+  uint32_t *sbs = ar.take<uint32_t>(hmax);
+  uint32_t *sbe = ar.take<uint32_t>(hmax);
+  uint32_t *edges = ar.take<uint32_t>(4);
   uint32_t *sbhalo = ar.take<uint32_t>(nbmax / 32 + 1);
   int4 *bmin = ar.take<int4>(nbmax);
   int4 *bmax = ar.take<int4>(nbmax);
@@ -658,50 +711,90 @@ vr_status run_velden(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Arena &a
     VR_TIMED(ctx, "velden_small", s, small(0, H));
     VR_LAUNCHED(ctx, "k_velden_small");
   }
-  k_sb_count<<<grid_for(H + 1, T), T, 0, s>>>(g.hoff, H, p->nse, sboff);
+  k_sb_count<<<grid_for(H + 1, T), T, 0, s>>>(g.hoff, g.horder, H, p->nse, sbr);
   VR_LAUNCHED(ctx, "k_sb_count");
-  VR_CUDA(ctx, exclusive_scan<uint32_t>(sboff, sboff, H + 1, scr, s));
-  VR_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned + 34, sboff + H, sizeof(uint32_t),
+  VR_CUDA(ctx, exclusive_scan<uint32_t>(sbr, sbr, H + 1, scr, s));
+  k_bin_edges<<<grid_for(H, T), T, 0, s>>>(g.hoff, g.horder, sbr, H, edges);
+  VR_LAUNCHED(ctx, "k_bin_edges");
+  VR_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned + 34, sbr + H, sizeof(uint32_t),
+                               cudaMemcpyDeviceToHost, s));
+  VR_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned + 35, edges, 2 * sizeof(uint32_t),
                                cudaMemcpyDeviceToHost, s));
   VR_CUDA(ctx, cudaStreamSynchronize(s));
-  uint32_t nsb = 0;
+  uint32_t nsb = 0, eg[2] = {0, 0};
   memcpy(&nsb, ctx->h_pinned + 34, 4);
+  memcpy(eg, ctx->h_pinned + 35, 8);
   if (nsb == 0) return VR_OK;
   int64_t nbpad = 32LL * nsb;
-  k_sb_fill<<<grid_for(H, T), T, 0, s>>>(sboff, H, sbhalo);
+  k_sb_fill<<<grid_for(H, T), T, 0, s>>>(sbr, g.horder, H, sbs, sbe, sbhalo);
   VR_LAUNCHED(ctx, "k_sb_fill");
-  k_bucket_boxes<<<grid_for(nbpad, T), T, 0, s>>>(g.hoff, sboff, sbhalo, nbpad, g.u, bmin, bmax);
+  k_bucket_boxes<<<grid_for(nbpad, T), T, 0, s>>>(g.hoff, sbs, sbhalo, nbpad, g.u, bmin, bmax);
   VR_LAUNCHED(ctx, "k_bucket_boxes");
   k_superbucket_boxes<<<grid_for(nsb, T), T, 0, s>>>(nsb, bmin, bmax, smin, smax);
   VR_LAUNCHED(ctx, "k_superbucket_boxes");
-  const size_t shm = (p->nv <= 32 ? sizeof(WarpSmem<32>) : sizeof(WarpSmem<kNVMax>)) * kWarps;
-  if (p->nv <= 32)
-    VR_CUDA(ctx, cudaFuncSetAttribute(k_velden_big<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-  else
-    VR_CUDA(ctx, cudaFuncSetAttribute(k_velden_big<kNVMax>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-  auto big = [&](int64_t a, int64_t z) {
-    if (p->nv <= 32)
-      k_velden_big<32><<<grid_for(z - a, kWarps), 32 * kWarps, shm, s>>>(
-          g.hoff, sboff, sbhalo, a, z, g.u, g.v, bmin, bmax, smin, smax, p->nse, p->nv, f_l,
-          ctx->d_status);
-    else
-      k_velden_big<kNVMax><<<grid_for(z - a, kWarps), 32 * kWarps, shm, s>>>(
-          g.hoff, sboff, sbhalo, a, z, g.u, g.v, bmin, bmax, smin, smax, p->nse, p->nv, f_l,
-          ctx->d_status);
+  const size_t wsm = p->nv <= 32 ? sizeof(WarpSmem<32>) : sizeof(WarpSmem<kNVMax>);
+  for (int sh = 0; sh < kNVShapes; ++sh) {
+    void *kf = p->nv <= 32 ? big_kernel<32>(sh) : big_kernel<kNVMax>(sh);
+    VR_CUDA(ctx, cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * wsm)));
+  }
+  // buckets [a, z) with launch shape `sh`
+  auto big = [&](int sh, int64_t a, int64_t z) -> cudaError_t {
+    const int w = p->nv <= 32 ? kVShapes[sh].warps : 4;
+    void *kf = p->nv <= 32 ? big_kernel<32>(sh) : big_kernel<kNVMax>(sh);
+    const int nse = p->nse, nv = p->nv;
+    DevStatus *st = ctx->d_status;
+    void *args[] = {(void *)&g.hoff, (void *)&sbs, (void *)&sbe, (void *)&sbhalo, (void *)&a,
+                    (void *)&z, (void *)&g.u, (void *)&g.v, (void *)&bmin, (void *)&bmax,
+                    (void *)&smin, (void *)&smax, (void *)&nse, (void *)&nv, (void *)&f_l,
+                    (void *)&st};
+    return cudaLaunchKernel(kf, dim3(grid_for(z - a, w)), dim3(32 * w), args, w * wsm, s);
   };
   if (hoff_host) {  // one launch per halo
-    std::vector<uint32_t> sb(H + 1);
-    VR_CUDA(ctx, cudaMemcpyAsync(sb.data(), sboff, (H + 1) * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    std::vector<uint32_t> s0(H), s1(H);
+    VR_CUDA(ctx, cudaMemcpyAsync(s0.data(), sbs, H * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    VR_CUDA(ctx, cudaMemcpyAsync(s1.data(), sbe, H * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     VR_CUDA(ctx, cudaStreamSynchronize(s));
     for (int64_t h = 0; h < H; ++h) {
-      if (sb[h + 1] == sb[h]) continue;
-      big(32LL * sb[h], 32LL * sb[h + 1]);
+      if (s1[h] == s0[h]) continue;
+      VR_CUDA(ctx, big(0, 32LL * s0[h], 32LL * s1[h]));
       VR_LAUNCHED(ctx, "k_velden_big");
     }
     return VR_OK;
   }
-  VR_TIMED(ctx, "velden_big", s, big(0, nbpad));
-  VR_LAUNCHED(ctx, "k_velden_big");
+  // one launch per halo-size bin, each with its own shape; a bin still to be tuned is
+  // run once per candidate shape (same results each time) and keeps the fastest
+  const int64_t lo[kVBins] = {0, 32LL * eg[0], 32LL * eg[1]};
+  const int64_t hi[kVBins] = {32LL * eg[0], 32LL * eg[1], nbpad};
+  timer_begin(ctx, "velden_big", s);
+  for (int k = 0; k < kVBins; ++k) {
+    if (hi[k] <= lo[k]) continue;
+    if (p->nv <= 32 && vmeasure(ctx, k)) {
+      Tuning *tn = ctx->tune;
+      cudaEvent_t e0, e1;
+      VR_CUDA(ctx, cudaEventCreate(&e0));
+      VR_CUDA(ctx, cudaEventCreate(&e1));
+      int best = 0;
+      for (int sh = 0; sh < kNVShapes; ++sh) {
+        VR_CUDA(ctx, cudaEventRecord(e0, s));
+        VR_CUDA(ctx, big(sh, lo[k], hi[k]));
+        VR_LAUNCHED(ctx, "k_velden_big");
+        VR_CUDA(ctx, cudaEventRecord(e1, s));
+        VR_CUDA(ctx, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        VR_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
+        tn->vms[k][sh] = ms;
+        if (ms < tn->vms[k][best]) best = sh;
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      tn->vshape[k] = best;
+      tn->vtuned[k] = 1;
+    } else {
+      VR_CUDA(ctx, big(p->nv <= 32 ? vshape_for(ctx, k) : 0, lo[k], hi[k]));
+      VR_LAUNCHED(ctx, "k_velden_big");
+    }
+  }
+  timer_end(ctx, "velden_big", s);
   return VR_OK;
 }
 

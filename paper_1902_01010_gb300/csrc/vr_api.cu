@@ -8,6 +8,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "tuning.cuh"
 #include "vr_internal.cuh"
 #include "vr_workspace.h"
 
@@ -201,6 +202,7 @@ vr_status vr_create(vr_ctx **out, int device) {
 void vr_destroy(vr_ctx *ctx) {
   if (!ctx) return;
   timers_free(ctx->timers);
+  delete ctx->tune;
   if (ctx->side) cudaStreamDestroy(ctx->side);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
@@ -268,5 +270,74 @@ vr_status vr_timing_reset(vr_ctx *ctx) {
 }
 
 int64_t vr_launch_count(void) { return (int64_t)g_launches.load(); }
+
+vr_status vr_autotune(vr_ctx *ctx, int enable) {
+  if (!ctx || (enable != 0 && enable != 1)) return VR_ERR_INVALID_ARG;
+  if (!ctx->tune) ctx->tune = new Tuning();
+  Tuning *t = ctx->tune;
+  t->on = enable;
+  for (int k = 0; k < kVBins; ++k) {
+    t->vtuned[k] = 0;
+    t->vshape[k] = 0;
+  }
+  t->ltuned = 0;
+  t->lshape = 0;
+  return VR_OK;
+}
+
+vr_status vr_tuning_force(vr_ctx *ctx, int velden_shape, int link_shape) {
+  if (!ctx || velden_shape < -1 || velden_shape >= kNVShapes || link_shape < -1 ||
+      link_shape >= kNLShapes)
+    return set_error(ctx, VR_ERR_INVALID_ARG, "shape index out of range");
+  if (!ctx->tune) ctx->tune = new Tuning();
+  ctx->tune->force_v = velden_shape;
+  ctx->tune->force_l = link_shape;
+  return VR_OK;
+}
+
+vr_status vr_tuning_report(const vr_ctx *ctx, char *buf, size_t len) {
+  if (!ctx || !buf || len == 0) return VR_ERR_INVALID_ARG;
+  Tuning none;
+  const Tuning *t = ctx->tune ? ctx->tune : &none;
+  std::string o = "{\"f_l\": {\"bins\": [\"> 65536\", \"4097-65536\", \"N_se+1-4096\"], "
+                  "\"shapes\": [";
+  char tmp[160];
+  for (int j = 0; j < kNVShapes; ++j) {
+    snprintf(tmp, sizeof(tmp), "%s{\"batch\": %d, \"maxreg\": %d, \"warps\": %d}", j ? ", " : "",
+             kVShapes[j].batch, kVShapes[j].maxreg, kVShapes[j].warps);
+    o += tmp;
+  }
+  o += "], \"chosen\": [";
+  for (int k = 0; k < kVBins; ++k) {
+    snprintf(tmp, sizeof(tmp), "%s%d", k ? ", " : "", vshape_for(ctx, k));
+    o += tmp;
+  }
+  o += "], \"measured\": [";
+  for (int k = 0; k < kVBins; ++k) {
+    o += k ? ", [" : "[";
+    for (int j = 0; j < kNVShapes; ++j) {
+      snprintf(tmp, sizeof(tmp), "%s%.4f", j ? ", " : "", t->vtuned[k] ? t->vms[k][j] : -1.0);
+      o += tmp;
+    }
+    o += "]";
+  }
+  o += "]}, \"link6\": {\"warps\": [";
+  for (int j = 0; j < kNLShapes; ++j) {
+    snprintf(tmp, sizeof(tmp), "%s%d", j ? ", " : "", kLWarps[j]);
+    o += tmp;
+  }
+  snprintf(tmp, sizeof(tmp), "], \"chosen\": %d, \"measured\": [", lshape_for(ctx));
+  o += tmp;
+  for (int j = 0; j < kNLShapes; ++j) {
+    snprintf(tmp, sizeof(tmp), "%s%.4f", j ? ", " : "", t->ltuned ? t->lms[j] : -1.0);
+    o += tmp;
+  }
+  snprintf(tmp, sizeof(tmp), "]}, \"tuning_on\": %d, \"forced\": [%d, %d]}", t->on, t->force_v,
+           t->force_l);
+  o += tmp;
+  if (o.size() + 1 > len) return VR_ERR_INVALID_ARG;
+  memcpy(buf, o.c_str(), o.size() + 1);
+  return VR_OK;
+}
 
 }  // extern "C"

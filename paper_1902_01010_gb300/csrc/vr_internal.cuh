@@ -27,6 +27,7 @@ struct DevStatus {
 
 namespace vr {
 struct Timers;  // per-kernel event timers (vr_api.cu)
+struct Tuning;  // launch shapes chosen by the autotuner (tuning.cuh)
 }
 
 struct vr_ctx {
@@ -36,6 +37,7 @@ struct vr_ctx {
   vr::DevStatus *d_status;  // device
   long long *h_pinned;      // pinned host staging (64 entries)
   vr::Timers *timers;       // NULL unless timing is enabled
+  vr::Tuning *tune;         // NULL until vr_autotune or vr_tuning_force is called
   cudaStream_t side;        // second stream for work that overlaps the caller's stream
   cudaEvent_t ev_fork, ev_join;
 };

@@ -27,7 +27,8 @@ EXPORTS = ("vr_params_default", "vr_create", "vr_destroy", "vr_last_error", "vr_
            "vr_sync", "vr_fof3d", "vr_velden", "vr_outlier_ratio", "vr_fof6d",
            "vr_fof6d_field", "vr_clean_groups", "vr_grow_params_default", "vr_grow_groups",
            "vr_core_params_default", "vr_core_search", "vr_core_grow_params_default",
-           "vr_core_grow", "vr_find_substructure")
+           "vr_core_grow", "vr_find_substructure", "vr_autotune", "vr_tuning_force",
+           "vr_tuning_report")
 
 
 class VrError(RuntimeError):
@@ -158,6 +159,9 @@ def lib(build_if_missing: bool = True):
                 "vr_find_substructure": (ctypes.c_int, [vp, vp, vp, i64, vp, dbl, dbl, P,
                                                         ctypes.c_int, vp, vp, vp, vp, vp,
                                                         ctypes.POINTER(i64), vp, sz, vp]),
+                "vr_autotune": (ctypes.c_int, [vp, ctypes.c_int]),
+                "vr_tuning_force": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int]),
+                "vr_tuning_report": (ctypes.c_int, [vp, ctypes.c_char_p, sz]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -214,6 +218,25 @@ class Context:
 
     def sync(self, stream=None):
         self.check(lib().vr_sync(self.h, _stream(stream)))
+
+    # ------------------------------------------------------------ launch shapes
+    def autotune(self, enable: bool = True):
+        """From the next call on, time every candidate launch shape of the f_l kernel (per
+        halo-size bin) and of the 6D linker on the caller's data and keep the fastest
+        (vr_autotune); False returns to the defaults."""
+        self.check(lib().vr_autotune(self.h, 1 if enable else 0))
+
+    def tuning_force(self, velden_shape: int = -1, link_shape: int = -1):
+        """Every later launch uses these shape indices (-1: not forced)."""
+        self.check(lib().vr_tuning_force(self.h, int(velden_shape), int(link_shape)))
+
+    def tuning_report(self) -> dict:
+        """Candidate shapes, the shapes in use and the measured ms (vr_tuning_report)."""
+        import json
+
+        buf = ctypes.create_string_buffer(8192)
+        self.check(lib().vr_tuning_report(self.h, buf, len(buf)))
+        return json.loads(buf.value.decode())
 
     # ------------------------------------------------------------------ calls
     def fof3d(self, pos: torch.Tensor, link_d2: int, label: torch.Tensor | None = None,
