@@ -71,33 +71,48 @@ struct SmallSmem {
   float top[NVM][32];
 };
 
-// Per-lane list of the nv smallest values (unsorted) with its current maximum.
+// Per-lane list of the nv smallest values, kept as a binary max-heap in the lane's
+// shared-memory column (top[0] is the largest kept value), with its size and maximum.
 struct TopV {
   int c, im;
   float m;
 };
 
+// Offers v to the list: while fewer than nv values are kept, v is added (sifted up);
+// after that v replaces the largest when it is smaller (sifted down from the root), so
+// a replacement costs log2(nv) steps instead of a scan of all nv values.
 __device__ __forceinline__ void top_insert(float (*top)[32], int lane, TopV &t, int nv, float v) {
   if (t.c < nv) {
-    top[t.c][lane] = v;
-    if (t.c == 0 || v > t.m) {
-      t.m = v;
-      t.im = t.c;
+    int i = t.c++;
+    while (i > 0) {
+      const int p = (i - 1) >> 1;
+      const float pv = top[p][lane];
+      if (pv >= v) break;
+      top[i][lane] = pv;
+      i = p;
     }
-    t.c++;
+    top[i][lane] = v;
+    t.m = top[0][lane];
   } else if (v < t.m) {
-    top[t.im][lane] = v;
-    float m = top[0][lane];
-    int im = 0;
-    for (int q = 1; q < nv; ++q) {
-      float x = top[q][lane];
-      if (x > m) {
-        m = x;
-        im = q;
+    int i = 0;
+    for (;;) {
+      const int l = 2 * i + 1;
+      if (l >= nv) break;
+      int ch = l;
+      float cv = top[l][lane];
+      if (l + 1 < nv) {
+        const float rv = top[l + 1][lane];
+        if (rv > cv) {
+          ch = l + 1;
+          cv = rv;
+        }
       }
+      if (cv <= v) break;
+      top[i][lane] = cv;
+      i = ch;
     }
-    t.m = m;
-    t.im = im;
+    top[i][lane] = v;
+    t.m = top[0][lane];
   }
 }
 
