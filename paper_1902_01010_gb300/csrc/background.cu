@@ -171,6 +171,7 @@ __global__ void __launch_bounds__(NT) k_cells_build(
   __shared__ uint32_t s_scan[NT];
   __shared__ unsigned long long s_keys[kSmallNode];
   __shared__ uint32_t s_wl[NT / 32], s_wr[NT / 32];
+  __shared__ int s_nleaves;
   if (first + (int64_t)blockIdx.x >= last) return;
   const int64_t h = horder[first + blockIdx.x];  // largest halos first
   const uint32_t hb = hoff[h], he = hoff[h + 1];
@@ -439,46 +440,59 @@ __global__ void __launch_bounds__(NT) k_cells_build(
     if (!split_done && t == 0) nd->axis = -1;
     __syncthreads();
   }
-  // leaves: FP64 moments and membership
-  int nleaves = 0;
+  // leaves: FP64 moments and membership, one warp per leaf (leaves taken round-robin by
+  // the block's warps; warp-shuffle reductions, so no block barrier per leaf)
+  if (t == 0) s_nleaves = 0;
+  __syncthreads();
   const int count = s_count;
-  for (int cur = 0; cur < count; ++cur) {
-    const CellNode *nd = &nodes[base + cur];
-    if (nd->axis >= 0) continue;
-    ++nleaves;
-    const uint32_t b = nd->beg, e = nd->end;
-    const double M = (double)(e - b);
-    long long sx[3] = {0, 0, 0};
-    double sv[3] = {0, 0, 0};
-    for (uint32_t i = b + t; i < e; i += NT) {
-      uint32_t m = perm[i];
-      leaf_of[m] = base + cur;
-      int4 p = u[m];
-      float4 q = v[m];
-      sx[0] += p.x; sx[1] += p.y; sx[2] += p.z;
-      sv[0] += (double)q.x; sv[1] += (double)q.y; sv[2] += (double)q.z;
-    }
-    double xm[3], vm[3];
-    for (int k = 0; k < 3; ++k) {
-      xm[k] = (double)block_reduce<NT>(sx[k], AddL(), s_rl) / M;
-      vm[k] = block_reduce<NT>(sv[k], AddD(), s_rd) / M;
-    }
-    double c[6] = {0, 0, 0, 0, 0, 0};
-    for (uint32_t i = b + t; i < e; i += NT) {
-      float4 q = v[perm[i]];
-      double d0 = (double)q.x - vm[0], d1 = (double)q.y - vm[1], d2 = (double)q.z - vm[2];
-      c[0] += d0 * d0; c[1] += d1 * d1; c[2] += d2 * d2;
-      c[3] += d0 * d1; c[4] += d0 * d2; c[5] += d1 * d2;
-    }
-    double S6[6];
-    for (int k = 0; k < 6; ++k) S6[k] = block_reduce<NT>(c[k], AddD(), s_rd) / M;
-    if (t == 0) {
-      double *o = mom + 13 * (int64_t)(base + cur);
-      o[0] = M;
-      for (int k = 0; k < 3; ++k) { o[1 + k] = xm[k]; o[4 + k] = vm[k]; }
-      for (int k = 0; k < 6; ++k) o[7 + k] = S6[k];
+  {
+    const int lane = t & 31, wid = t >> 5;
+    const unsigned FULL = 0xffffffffu;
+    for (int cur = wid; cur < count; cur += NT / 32) {
+      const CellNode *nd = &nodes[base + cur];
+      if (nd->axis >= 0) continue;  // the same node for the whole warp
+      if (lane == 0) atomicAdd(&s_nleaves, 1);
+      const uint32_t b = nd->beg, e = nd->end;
+      const double M = (double)(e - b);
+      long long sx[3] = {0, 0, 0};
+      double sv[3] = {0, 0, 0};
+      for (uint32_t i = b + lane; i < e; i += 32) {
+        const uint32_t m = perm[i];
+        leaf_of[m] = base + cur;
+        const int4 p = u[m];
+        const float4 q = v[m];
+        sx[0] += p.x; sx[1] += p.y; sx[2] += p.z;
+        sv[0] += (double)q.x; sv[1] += (double)q.y; sv[2] += (double)q.z;
+      }
+      for (int o = 16; o; o >>= 1)
+        for (int k = 0; k < 3; ++k) {
+          sx[k] += __shfl_xor_sync(FULL, sx[k], o);
+          sv[k] += __shfl_xor_sync(FULL, sv[k], o);
+        }
+      double xm[3], vm[3];
+      for (int k = 0; k < 3; ++k) {
+        xm[k] = (double)sx[k] / M;
+        vm[k] = sv[k] / M;
+      }
+      double c[6] = {0, 0, 0, 0, 0, 0};
+      for (uint32_t i = b + lane; i < e; i += 32) {
+        const float4 q = v[perm[i]];
+        const double d0 = (double)q.x - vm[0], d1 = (double)q.y - vm[1], d2 = (double)q.z - vm[2];
+        c[0] += d0 * d0; c[1] += d1 * d1; c[2] += d2 * d2;
+        c[3] += d0 * d1; c[4] += d0 * d2; c[5] += d1 * d2;
+      }
+      for (int o = 16; o; o >>= 1)
+        for (int k = 0; k < 6; ++k) c[k] += __shfl_xor_sync(FULL, c[k], o);
+      if (lane == 0) {
+        double *out = mom + 13 * (int64_t)(base + cur);
+        out[0] = M;
+        for (int k = 0; k < 3; ++k) { out[1 + k] = xm[k]; out[4 + k] = vm[k]; }
+        for (int k = 0; k < 6; ++k) out[7 + k] = c[k] / M;
+      }
     }
   }
+  __syncthreads();
+  const int nleaves = s_nleaves;
   if (t == 0) hs_out[h * VR_HALO_COLS + VR_H_NCELLS] = (double)nleaves;
 }
 
