@@ -33,7 +33,6 @@ constexpr int kSmallT = 256;       // threads per tree-building CTA, halos below
 constexpr int kBigT = 1024;        // threads per tree-building CTA, halos of kBigHalo or more
 constexpr int64_t kBigHalo = 65536;
 constexpr int kMaxBins = 162;      // floor((2^22)^(1/3)) + 1
-constexpr int kSmallNode = 1024;   // nodes up to this size find their median by counting
 
 __device__ __forceinline__ int64_t ncell_of(int64_t nh, double f_cell, int ncell_min) {
   int64_t nc = (int64_t)floor(__dmul_rn(f_cell, (double)nh));
@@ -67,7 +66,6 @@ __device__ __forceinline__ T block_reduce(T v, Op op, T *sbuf) {
 
 struct MinOp { __device__ int operator()(int a, int b) const { return a < b ? a : b; } };
 struct MaxOp { __device__ int operator()(int a, int b) const { return a > b ? a : b; } };
-struct AddL { __device__ long long operator()(long long a, long long b) const { return a + b; } };
 struct AddD { __device__ double operator()(double a, double b) const { return a + b; } };
 struct AddI { __device__ int operator()(int a, int b) const { return a + b; } };
 
@@ -150,6 +148,228 @@ __global__ void k_node_caps(const uint32_t *__restrict__ hoff, int64_t H, int ns
   caps[h] = (uint32_t)(kNodeFactor * ((nh + nc) / (nc + 1)) + 16);
 }
 
+constexpr int kStackCap = 128;  // depth of a warp's node stack
+// Per-warp scratch of the tree build (dynamic shared memory, one per warp): axis
+// histograms, the radix digit counts of a median selection and the warp's node stack.
+struct WarpTree {
+  int hist[3][kMaxBins];
+  uint32_t dig[256];
+  int stack[kStackCap];
+};
+constexpr int kPendCap = 256;  // nodes handed from the block to its warps
+
+// The digit holding the need-th (1-based) key of a warp's 256 digit counts and the
+// number of keys in the digits below it (warp-uniform).
+__device__ __forceinline__ int warp_digit(const uint32_t *dig, int lane, uint32_t need,
+                                          uint32_t *below) {
+  uint32_t c[8], tot = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    c[i] = dig[8 * lane + i];
+    tot += c[i];
+  }
+  uint32_t inc = tot;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  const unsigned m = __ballot_sync(0xffffffffu, inc >= need);
+  const int L = m ? __ffs(m) - 1 : 31;
+  uint32_t run = inc - tot, bel = run;
+  int bin = 8 * lane + 7;
+  bool done = false;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    if (!done && run + c[i] >= need) {
+      bin = 8 * lane + i;
+      bel = run;
+      done = true;
+    }
+    run += c[i];
+  }
+  *below = __shfl_sync(0xffffffffu, bel, L);
+  return __shfl_sync(0xffffffffu, bin, L);
+}
+
+// Splits the subtree rooted at node `root` of one halo with a single warp, depth first:
+// the same rules as the block path (entropy of n_b bins per axis, axis order by S with
+// ties within 1e-12 to the lower axis, split at element floor(n/2) in (coordinate, local
+// index) order, left = {x < split}, an axis leaving the left side empty skipped, stable
+// partition), with warp shuffles and per-warp shared counts instead of block barriers.
+// New nodes are numbered by an atomic counter; results do not depend on the numbering.
+__device__ void warp_build(int root, uint32_t base, uint32_t cap, int64_t ncell, int split_rule,
+                           const int4 *__restrict__ u, uint32_t *__restrict__ perm,
+                           uint32_t *__restrict__ tmp, CellNode *__restrict__ nodes,
+                           int *s_count, WarpTree &wt, DevStatus *st) {
+  const int lane = threadIdx.x & 31;
+  const unsigned FULL = 0xffffffffu, lt = (1u << lane) - 1u;
+  int sp = 0;
+  if (lane == 0) wt.stack[0] = root;
+  sp = 1;
+  __syncwarp();
+  while (sp > 0) {
+    const int id = wt.stack[--sp];
+    __syncwarp();
+    CellNode *nd = &nodes[base + id];
+    const uint32_t nb_ = nd->beg, ne_ = nd->end;
+    const int64_t n = ne_ - nb_;
+    if (n <= ncell) {
+      if (lane == 0) nd->axis = -1;
+      continue;
+    }
+    int amin[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff}, amax[3] = {-0x7fffffff, -0x7fffffff, -0x7fffffff};
+    for (uint32_t i = nb_ + lane; i < ne_; i += 32) {
+      const int4 p = u[perm[i]];
+      amin[0] = min(amin[0], p.x); amin[1] = min(amin[1], p.y); amin[2] = min(amin[2], p.z);
+      amax[0] = max(amax[0], p.x); amax[1] = max(amax[1], p.y); amax[2] = max(amax[2], p.z);
+    }
+    for (int o = 16; o; o >>= 1)
+      for (int a = 0; a < 3; ++a) {
+        amin[a] = min(amin[a], __shfl_xor_sync(FULL, amin[a], o));
+        amax[a] = max(amax[a], __shfl_xor_sync(FULL, amax[a], o));
+      }
+    const int64_t nbins = max((int64_t)2, icbrt_dev(n));
+    for (int k = lane; k < 3 * kMaxBins; k += 32) (&wt.hist[0][0])[k] = 0;
+    __syncwarp();
+    for (uint32_t i = nb_ + lane; i < ne_; i += 32) {
+      const int4 p = u[perm[i]];
+      for (int a = 0; a < 3; ++a)
+        if (amax[a] > amin[a]) {
+          const int64_t bin = ((int64_t)(coord(p, a) - amin[a]) * nbins) / ((int64_t)amax[a] - amin[a] + 1);
+          atomicAdd(&wt.hist[a][bin], 1);
+        }
+    }
+    __syncwarp();
+    // Shannon entropy per axis (Eq. S); every lane ends with the same sums
+    double S[3];
+    int ok[3];
+    for (int a = 0; a < 3; ++a) {
+      ok[a] = amax[a] > amin[a];
+      double part = 0.0;
+      if (ok[a])
+        for (int b = lane; b < nbins; b += 32) {
+          const int c = wt.hist[a][b];
+          if (c > 0) {
+            const double f = (double)c / (double)n;
+            part -= f * log(f);
+          }
+        }
+      for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
+      S[a] = ok[a] ? part / log((double)nbins) : 0.0;
+    }
+    int order[3], norder = 0, used[3] = {0, 0, 0};
+    for (int r = 0; r < 3; ++r) {
+      int best = -1;
+      for (int a = 0; a < 3; ++a) {
+        if (!ok[a] || used[a]) continue;
+        if (best < 0) { best = a; continue; }
+        if (split_rule == 0 ? (S[a] > S[best] + 1e-12) : (S[a] < S[best] - 1e-12)) best = a;
+      }
+      if (best < 0) break;
+      used[best] = 1;
+      order[norder++] = best;
+    }
+    bool split_done = false;
+    for (int r = 0; r < norder && !split_done; ++r) {
+      const int a = order[r];
+      const int lo_a = amin[a];
+      auto node_key = [&](uint32_t i) {
+        const int4 p = u[perm[i]];
+        return ((unsigned long long)(coord(p, a) - lo_a) << 22) | (unsigned)p.w;
+      };
+      // element of rank floor(n/2) by 8-bit radix selection from the top digit
+      int bits = 22;
+      {
+        unsigned int ext = (unsigned int)(amax[a] - lo_a);
+        while (ext) { ++bits; ext >>= 1; }
+      }
+      unsigned long long prefix = 0ULL;
+      uint32_t rank = (uint32_t)(n / 2);
+      for (int d = (bits + 7) / 8 - 1; d >= 0; --d) {
+        const int sh = 8 * d;
+        for (int k = lane; k < 256; k += 32) wt.dig[k] = 0u;
+        __syncwarp();
+        for (uint32_t i = nb_ + lane; i < ne_; i += 32) {
+          const unsigned long long key = node_key(i);
+          const unsigned long long hk = (sh + 8 >= 64) ? 0ULL : (key >> (sh + 8));
+          const unsigned long long hp = (sh + 8 >= 64) ? 0ULL : (prefix >> (sh + 8));
+          if (hk == hp) atomicAdd(&wt.dig[(key >> sh) & 0xffu], 1u);
+        }
+        __syncwarp();
+        uint32_t below;
+        const int dg = warp_digit(wt.dig, lane, rank + 1u, &below);
+        prefix |= (unsigned long long)dg << sh;
+        rank -= below;
+        __syncwarp();
+      }
+      const int xs = lo_a + (int)(prefix >> 22);
+      int cl = 0;
+      for (uint32_t i = nb_ + lane; i < ne_; i += 32) cl += coord(u[perm[i]], a) < xs ? 1 : 0;
+      for (int o = 16; o; o >>= 1) cl += __shfl_xor_sync(FULL, cl, o);
+      const int nleft = cl;
+      if (nleft == 0) continue;  // left side empty: next axis
+      // stable partition: chunks of 32 in the node's order, left block then right block
+      uint32_t offl = 0, offr = 0;
+      for (uint32_t cb = nb_; cb < ne_; cb += 32) {
+        const uint32_t i = cb + lane;
+        const bool okm = i < ne_;
+        uint32_t pm = 0;
+        bool isl = false;
+        if (okm) {
+          pm = perm[i];
+          isl = coord(u[pm], a) < xs;
+        }
+        const unsigned bl = __ballot_sync(FULL, okm && isl);
+        const unsigned br = __ballot_sync(FULL, okm && !isl);
+        if (okm) {
+          if (isl) tmp[nb_ + offl + __popc(bl & lt)] = pm;
+          else tmp[nb_ + nleft + offr + __popc(br & lt)] = pm;
+        }
+        offl += __popc(bl);
+        offr += __popc(br);
+      }
+      __syncwarp();
+      for (uint32_t i = nb_ + lane; i < ne_; i += 32) perm[i] = tmp[i];
+      __syncwarp();
+      int c0 = 0;
+      if (lane == 0) {
+        c0 = sp + 2 <= kStackCap ? atomicAdd(s_count, 2) : (int)cap;  // stack full: error
+        if ((uint32_t)(c0 + 2) > cap) {
+          raise_error(st, VR_ERR_UNSUPPORTED, 3);
+          nd->axis = -1;
+          c0 = -1;
+        } else {
+          CellNode *L = &nodes[base + c0], *R = &nodes[base + c0 + 1];
+          for (int k = 0; k < 3; ++k) {
+            L->lo[k] = R->lo[k] = nd->lo[k];
+            L->hi[k] = R->hi[k] = nd->hi[k];
+          }
+          L->hi[a] = xs;
+          R->lo[a] = xs;
+          L->beg = nb_;
+          L->end = nb_ + nleft;
+          R->beg = nb_ + nleft;
+          R->end = ne_;
+          L->axis = R->axis = -1;
+          nd->axis = a;
+          nd->split = xs;
+          nd->left = c0;
+          nd->right = c0 + 1;
+          wt.stack[sp] = c0 + 1;
+          wt.stack[sp + 1] = c0;
+        }
+      }
+      c0 = __shfl_sync(FULL, c0, 0);
+      if (c0 >= 0) sp += 2;
+      __syncwarp();
+      split_done = true;
+    }
+    if (!split_done && lane == 0) nd->axis = -1;
+    __syncwarp();
+  }
+}
+
 template <int NT>
 __global__ void __launch_bounds__(NT) k_cells_build(
     const uint32_t *__restrict__ hoff, const uint32_t *__restrict__ horder,
@@ -161,7 +381,6 @@ __global__ void __launch_bounds__(NT) k_cells_build(
   __shared__ int s_hist[3][kMaxBins];
   __shared__ uint32_t s_dig[256];
   __shared__ int s_ri[NT / 32];
-  __shared__ long long s_rl[NT / 32];
   __shared__ double s_rd[NT / 32];
   __shared__ int s_order[3];
   __shared__ int s_norder;
@@ -169,7 +388,9 @@ __global__ void __launch_bounds__(NT) k_cells_build(
   __shared__ int s_rank;
   __shared__ int s_count;
   __shared__ uint32_t s_scan[NT];
-  __shared__ unsigned long long s_keys[kSmallNode];
+  __shared__ int s_pend[kPendCap];
+  __shared__ int s_npend;
+  extern __shared__ __align__(16) unsigned char tree_smem[];
   __shared__ uint32_t s_wl[NT / 32], s_wr[NT / 32];
   __shared__ int s_nleaves;
   if (first + (int64_t)blockIdx.x >= last) return;
@@ -205,7 +426,11 @@ __global__ void __launch_bounds__(NT) k_cells_build(
       s_count = 1;
     }
   }
+  if (t == 0) s_npend = 0;
   __syncthreads();
+  // nodes of at most `tw` members are split by single warps afterwards (whole subtrees);
+  // larger ones by the whole block, one at a time
+  const int64_t tw = max((int64_t)1024, nh / (2 * (NT / 32)));
   for (int cur = 0; cur < s_count; ++cur) {
     CellNode *nd = &nodes[base + cur];
     const uint32_t nb_ = nd->beg, ne_ = nd->end;
@@ -213,6 +438,13 @@ __global__ void __launch_bounds__(NT) k_cells_build(
     __syncthreads();
     if (n <= ncell) {
       if (t == 0) nd->axis = -1;
+      __syncthreads();
+      continue;
+    }
+    const bool hand = n <= tw && s_npend < kPendCap;  // read by every thread before the write
+    __syncthreads();
+    if (hand) {
+      if (t == 0) s_pend[s_npend++] = cur;
       __syncthreads();
       continue;
     }
@@ -291,19 +523,7 @@ __global__ void __launch_bounds__(NT) k_cells_build(
         int4 p = u[perm[i]];
         return ((unsigned long long)(coord(p, a) - lo_a) << 22) | (unsigned)p.w;
       };
-      if (n <= kSmallNode) {
-        // small node: rank by counting, keys staged in shared memory
-        for (uint32_t i = nb_ + t; i < ne_; i += NT) s_keys[i - nb_] = node_key(i);
-        __syncthreads();
-        const int target = (int)(n / 2);
-        for (int i = t; i < (int)n; i += NT) {
-          const unsigned long long ki = s_keys[i];
-          int below = 0;
-          for (int j = 0; j < (int)n; ++j) below += s_keys[j] < ki ? 1 : 0;
-          if (below == target) s_prefix = ki;
-        }
-        __syncthreads();
-      } else {
+      {
         // large node: 8-bit radix selection from the top digit
         int bits = 22;
         {
@@ -439,6 +659,14 @@ __global__ void __launch_bounds__(NT) k_cells_build(
     }
     if (!split_done && t == 0) nd->axis = -1;
     __syncthreads();
+  }
+  // the handed-over nodes: one warp builds each subtree
+  __syncthreads();
+  {
+    WarpTree &wt = reinterpret_cast<WarpTree *>(tree_smem)[t >> 5];
+    const int np = s_npend;
+    for (int k = t >> 5; k < np; k += NT / 32)
+      warp_build(s_pend[k], base, cap, ncell, split_rule, u, perm, tmp, nodes, &s_count, wt, st);
   }
   // leaves: FP64 moments and membership, one warp per leaf (leaves taken round-robin by
   // the block's warps; warp-shuffle reductions, so no block barrier per leaf)
@@ -655,14 +883,17 @@ vr_status run_background(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Aren
                                                    p->ncell_min, bg.nodeoff);
   VR_LAUNCHED(ctx, "k_node_caps");
   VR_CUDA(ctx, exclusive_scan<uint32_t>(bg.nodeoff, bg.nodeoff, H + 1, scr, s));
+  const size_t smem_big = sizeof(WarpTree) * (kBigT / 32), smem_small = sizeof(WarpTree) * (kSmallT / 32);
+  VR_CUDA(ctx, cudaFuncSetAttribute(k_cells_build<kBigT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_big));
+  VR_CUDA(ctx, cudaFuncSetAttribute(k_cells_build<kSmallT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_small));
   auto build = [&](bool bigc, cudaStream_t st, int64_t a, int64_t z, unsigned grid) {
     if (bigc)
-      k_cells_build<kBigT><<<grid, kBigT, 0, st>>>(g.hoff, g.horder, bg.nodeoff, a, z, g.u, g.v,
+      k_cells_build<kBigT><<<grid, kBigT, smem_big, st>>>(g.hoff, g.horder, bg.nodeoff, a, z, g.u, g.v,
                                                    p->nsearch_min, p->f_cell, p->ncell_min,
                                                    p->split_rule, perm, tmp, bg.nodes, bg.mom,
                                                    bg.leaf_of, halo_stats, ctx->d_status);
     else
-      k_cells_build<kSmallT><<<grid, kSmallT, 0, st>>>(g.hoff, g.horder, bg.nodeoff, a, z, g.u,
+      k_cells_build<kSmallT><<<grid, kSmallT, smem_small, st>>>(g.hoff, g.horder, bg.nodeoff, a, z, g.u,
                                                        g.v, p->nsearch_min, p->f_cell,
                                                        p->ncell_min, p->split_rule, perm, tmp,
                                                        bg.nodes, bg.mom, bg.leaf_of, halo_stats,
