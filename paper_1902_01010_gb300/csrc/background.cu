@@ -922,7 +922,7 @@ vr_status run_background(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Aren
   }
   // Halos of kBigHalo members or more (the first entries of the size order) run with
   // 1024-thread CTAs on the context's side stream while all other halos run with
-  // 256-thread CTAs on the caller's stream; the two launches overlap.
+  // 256-thread CTAs on stream s; the two launches overlap.
   const int64_t nbig_max = g.NHP / kBigHalo + 1;
   const unsigned big_grid = (unsigned)(nbig_max < H ? nbig_max : H);
   VR_CUDA(ctx, cudaEventRecord(ctx->ev_fork, s));
@@ -933,6 +933,14 @@ vr_status run_background(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Aren
   VR_LAUNCHED(ctx, "k_cells_build");
   VR_CUDA(ctx, cudaEventRecord(ctx->ev_join, ctx->side));
   VR_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev_join, 0));
+  if (f_l) return background_ratio(ctx, g, bg, f_l, R, s);
+  return VR_OK;
+}
+
+vr_status background_ratio(vr_ctx *ctx, const HaloSeg &g, const Background &bg, const float *f_l,
+                           float *R, cudaStream_t s) {
+  if (g.H == 0) return VR_OK;
+  unsigned long long *ndeg = (unsigned long long *)&ctx->d_status->info[0];
   VR_TIMED(ctx, "ratio", s, k_ratio<<<grid_for(g.NHP, 256), 256, 0, s>>>(g.hid, bg.nodeoff, 0, g.NHP, g.u, g.v, f_l, bg.nodes,
                                                bg.mom, bg.leaf_of, R, ndeg));
   VR_LAUNCHED(ctx, "k_ratio");

@@ -26,7 +26,12 @@ struct Background {
 
 int64_t max_nodes(int64_t n, const vr_params *p);
 size_t background_bytes(int64_t n, const vr_params *p);
+// Halo frames, cell trees and moments, then R (Eq. fvbg). With f_l == NULL (batched form
+// only) the R kernel is left to background_ratio, so that the tree build can run beside
+// the f_l stage on another stream.
 vr_status run_background(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Arena &ar,
                          const float *f_l, float *R, double *halo_stats, Background *out,
                          cudaStream_t s, const uint32_t *hoff_host = nullptr);
+vr_status background_ratio(vr_ctx *ctx, const HaloSeg &g, const Background &bg, const float *f_l,
+                           float *R, cudaStream_t s);
 }  // namespace vr

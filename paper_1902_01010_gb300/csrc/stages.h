@@ -4,7 +4,7 @@
 #include "background.cuh"
 
 namespace vr {
-size_t velden_bytes(int64_t n, int nmin);
+size_t velden_bytes(int64_t n, int nmin, int nse);
 // hoff_host / plain: non-NULL / true selects one launch per halo (the plain form)
 vr_status run_velden(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Arena &ar, float *f_l,
                      cudaStream_t s, const uint32_t *hoff_host = nullptr);

@@ -11,8 +11,9 @@
 namespace vr {
 
 size_t ws_substructure(int64_t n, const vr_params *p) {
-  size_t a = velden_bytes(n, p->nmin), b = background_bytes(n, p), c = fof6d_bytes(n, p->nmin);
-  size_t m = a > b ? a : b;
+  // the f_l stage and the cell trees run side by side in the batched form: both regions
+  size_t a = velden_bytes(n, p->nmin, p->nse), b = background_bytes(n, p), c = fof6d_bytes(n, p->nmin);
+  size_t m = a + b;
   m = m > c ? m : c;
   const size_t t = halo_seg_temp_bytes(n, p->nmin);
   m = m > t ? m : t;
@@ -321,10 +322,23 @@ vr_status vr_find_substructure(vr_ctx *ctx, const int32_t *pos, const float *vel
   }
   const uint32_t *hh = plain ? hoff_host.data() : nullptr;
   const size_t mark = ar.off;
-  if ((st = run_velden(ctx, g, p, ar, f_l, s, hh)) != VR_OK) return st;
-  ar.off = mark;
   Background bg;
-  if ((st = run_background(ctx, g, p, ar, f_l, R, halo_stats, &bg, s, hh)) != VR_OK) return st;
+  if (plain) {
+    if ((st = run_velden(ctx, g, p, ar, f_l, s, hh)) != VR_OK) return st;
+    ar.off = mark;
+    if ((st = run_background(ctx, g, p, ar, f_l, R, halo_stats, &bg, s, hh)) != VR_OK) return st;
+  } else {
+    // the halo frames and cell trees need only the segmentation: they run on a third
+    // stream while the f_l kernels run on `s` (separate workspace regions); R waits for both
+    VR_CUDA(ctx, cudaEventRecord(ctx->ev_fork2, s));
+    VR_CUDA(ctx, cudaStreamWaitEvent(ctx->side2, ctx->ev_fork2, 0));
+    if ((st = run_background(ctx, g, p, ar, nullptr, R, halo_stats, &bg, ctx->side2)) != VR_OK)
+      return st;
+    VR_CUDA(ctx, cudaEventRecord(ctx->ev_join2, ctx->side2));
+    if ((st = run_velden(ctx, g, p, ar, f_l, s)) != VR_OK) return st;
+    VR_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev_join2, 0));
+    if ((st = background_ratio(ctx, g, bg, f_l, R, s)) != VR_OK) return st;
+  }
   if ((st = run_fit(ctx, g, bg, p, R, halo_stats, ell, s, hh)) != VR_OK) return st;
   ar.off = mark;
   if (g.H > 0) {

@@ -656,10 +656,14 @@ __global__ void k_fill_f32(float *__restrict__ a, int64_t n, float val) {
 
 }  // namespace
 
-size_t velden_bytes(int64_t n, int nmin) {
+// Buckets with their padding: a halo of more than N_se members pads its buckets to a
+// multiple of 32, at most 31 per such halo.
+inline int64_t bucket_bound(int64_t n, int nse) { return n / 32 + 32 * (n / (nse + 1) + 2) + 64; }
+
+size_t velden_bytes(int64_t n, int nmin, int nse) {
   Arena ar;
   int64_t hmax = n / (nmin > 0 ? nmin : 1) + 2;
-  int64_t nbmax = n / 32 + 32 * hmax + 64;  // padded buckets
+  int64_t nbmax = bucket_bound(n, nse);
   ar.take<uint32_t>(hmax + 1);  // sbr
   ar.take<uint32_t>(hmax);      // sbs
   ar.take<uint32_t>(hmax);      // sbe
@@ -696,7 +700,7 @@ vr_status run_velden(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Arena &a
   if (g.H == 0) return VR_OK;
   const int64_t H = g.H;
   int64_t hmax = g.n / (p->nmin > 0 ? p->nmin : 1) + 2;
-  int64_t nbmax = g.n / 32 + 32 * hmax + 64;
+  int64_t nbmax = bucket_bound(g.n, p->nse);
   uint32_t *sbr = ar.take<uint32_t>(hmax + 1);
   uint32_t *sbs = ar.take<uint32_t>(hmax);
   uint32_t *sbe = ar.take<uint32_t>(hmax);

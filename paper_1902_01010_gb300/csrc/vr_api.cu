@@ -190,6 +190,9 @@ vr_status vr_create(vr_ctx **out, int device) {
       cudaMallocHost(&c->h_pinned, 64 * sizeof(long long)) != cudaSuccess ||
       cudaMemset(c->d_status, 0, sizeof(DevStatus)) != cudaSuccess ||
       cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->side2, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_fork2, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
     vr_destroy(c);
@@ -204,6 +207,9 @@ void vr_destroy(vr_ctx *ctx) {
   timers_free(ctx->timers);
   delete ctx->tune;
   if (ctx->side) cudaStreamDestroy(ctx->side);
+  if (ctx->side2) cudaStreamDestroy(ctx->side2);
+  if (ctx->ev_fork2) cudaEventDestroy(ctx->ev_fork2);
+  if (ctx->ev_join2) cudaEventDestroy(ctx->ev_join2);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   if (ctx->d_status) cudaFree(ctx->d_status);

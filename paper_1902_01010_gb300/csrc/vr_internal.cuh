@@ -40,6 +40,8 @@ struct vr_ctx {
   vr::Tuning *tune;         // NULL until vr_autotune or vr_tuning_force is called
   cudaStream_t side;        // second stream for work that overlaps the caller's stream
   cudaEvent_t ev_fork, ev_join;
+  cudaStream_t side2;       // third stream: the cell-tree build beside the f_l stage
+  cudaEvent_t ev_fork2, ev_join2;
 };
 
 namespace vr {
