@@ -165,8 +165,10 @@ VELDEN_OPS_PER_QUERY = 256 * 8 + 256 * 8 + 256 + 256 + 32 * 3
 # + dram__bytes_write.sum of one launch over its query particles); the kernel's traffic
 # grows with its queries, so a full launch is this times its queries. None whenever the
 # kernel has changed since the capture.
-VELDEN_DRAM_BYTES_PER_QUERY = None
-VELDEN_DRAM_SOURCE = None
+VELDEN_DRAM_BYTES_PER_QUERY = 3866411264 / 39635926
+VELDEN_DRAM_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the three per-bin "
+                      "k_velden_big launches of one 512^3 step (3.87 GB over 39,635,926 query "
+                      "particles), times this step's query particles")
 LANES_PER_SM = 128  # FP32/INT32 lanes per SM (4 partitions x 32)
 
 
