@@ -520,7 +520,7 @@ def run_ours(args):
 
     cpu, parity = None, None
     if not args.no_cpu_baseline and not prelab:
-        cpu, parity = cpu_leg(box, ctx, dev, lab, out, hs_np, P)
+        cpu, parity = cpu_leg(box, ctx, dev, lab, out, hs_np, P, args.workload)
     line = {
         "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -590,7 +590,7 @@ def _halo_gpu(out, members_t, hs_row):
     return g
 
 
-def cpu_leg(box, ctx, dev, lab_t, out, hs_np, P):
+def cpu_leg(box, ctx, dev, lab_t, out, hs_np, P, wname):
     """The oracle timed on a bounded sample of this box (rank 0, after the timed region),
     with the parity report of the same sample. Returns (cpu_baseline, parity)."""
     import torch
@@ -671,8 +671,8 @@ def cpu_leg(box, ctx, dev, lab_t, out, hs_np, P):
     flips = [dict(f, halo=r["label"], band=r["band"]) for r in srch_recs for f in r["flips"]]
     near = [p for r in srch_recs + big for p in r["near_threshold"]["pairs"]]
     parity = {
-        "c512_sampled": {
-            "halos": len(halos) + len(big), "searched_halos": len(srch_recs) + len(big),
+        "sampled": {
+            "box": wname, "halos": len(halos) + len(big), "searched_halos": len(srch_recs) + len(big),
             "independent": {
                 "f_l_max_rel": mx("f_l_max_rel", halos + big),
                 "R_max_rel": mx("R_max_rel", srch_recs),
