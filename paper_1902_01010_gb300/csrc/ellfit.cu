@@ -115,10 +115,17 @@ __device__ __forceinline__ double warp_sum(double x) {
   return x;
 }
 
-__device__ bool solve4(double M[4][4], const double *b, double *x) {
+// Solves (JtJ + lambda diag(JtJ)) x = b by Gaussian elimination with partial pivoting;
+// jj holds the upper triangle of JtJ row by row.
+__device__ bool solve4(const double *jj, double lambda, const double *b, double *x) {
   double a[4][5];
+  int q = 0;
+  for (int i = 0; i < 4; ++i)
+    for (int j = i; j < 4; ++j) {
+      a[i][j] = a[j][i] = jj[q++];
+    }
   for (int i = 0; i < 4; ++i) {
-    for (int j = 0; j < 4; ++j) a[i][j] = M[i][j];
+    a[i][i] = a[i][i] + lambda * a[i][i];
     a[i][4] = b[i];
   }
   for (int c = 0; c < 4; ++c) {
@@ -295,43 +302,51 @@ __global__ void __launch_bounds__(kFT, VR_FIT_MINB) k_ell_fit(const uint32_t *__
     }
     cost = warp_sum(cost);
     double lambda = 1e-3;
+    // J^T J and J^T r depend on p alone: after a rejected step (p unchanged) the sums of
+    // the previous iteration are reused as they are
+    double jj[10], jr[4];
+    bool fresh = true;
     for (int it = 0; it < iters; ++it) {
-      double jj[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0}, jr[4] = {0, 0, 0, 0};
-      for (int b = lane; b < nb; b += 32) {
-        double g[4];
-        double r = (double)s_cnt[b] - sg_eval(center(b), p, g);
-        int q = 0;
-        for (int i = 0; i < 4; ++i) {
-          jr[i] += g[i] * r;
-          for (int j = i; j < 4; ++j) jj[q++] += g[i] * g[j];
+      if (fresh) {
+        for (int q = 0; q < 10; ++q) jj[q] = 0.0;
+        for (int i = 0; i < 4; ++i) jr[i] = 0.0;
+        for (int b = lane; b < nb; b += 32) {
+          double g[4];
+          double r = (double)s_cnt[b] - sg_eval(center(b), p, g);
+          int q = 0;
+          for (int i = 0; i < 4; ++i) {
+            jr[i] += g[i] * r;
+            for (int j = i; j < 4; ++j) jj[q++] += g[i] * g[j];
+          }
         }
+        for (int q = 0; q < 10; ++q) jj[q] = warp_sum(jj[q]);
+        for (int i = 0; i < 4; ++i) jr[i] = warp_sum(jr[i]);
+        fresh = false;
       }
-      for (int q = 0; q < 10; ++q) jj[q] = warp_sum(jj[q]);
-      for (int i = 0; i < 4; ++i) jr[i] = warp_sum(jr[i]);
-      double M[4][4];
-      int q = 0;
-      for (int i = 0; i < 4; ++i)
-        for (int j = i; j < 4; ++j) {
-          M[i][j] = M[j][i] = jj[q++];
-        }
-      for (int i = 0; i < 4; ++i) M[i][i] = M[i][i] + lambda * M[i][i];
       double delta[4] = {0, 0, 0, 0};
-      bool ok = solve4(M, jr, delta);
+      bool ok = solve4(jj, lambda, jr, delta);
       double qp[4];
       for (int i = 0; i < 4; ++i) qp[i] = p[i] + (ok ? delta[i] : 0.0);
       double ncost = INFINITY;
       if (ok && qp[2] > 0.0 && qp[3] > 0.0) {
-        ncost = 0.0;
-        for (int b = lane; b < nb; b += 32) {
-          double r = (double)s_cnt[b] - sg_eval(center(b), qp, nullptr);
-          ncost += r * r;
+        bool same = true;  // a step lost to rounding: the cost at qp is the cost at p
+        for (int i = 0; i < 4; ++i) same &= __double_as_longlong(qp[i]) == __double_as_longlong(p[i]);
+        if (same) {
+          ncost = cost;
+        } else {
+          ncost = 0.0;
+          for (int b = lane; b < nb; b += 32) {
+            double r = (double)s_cnt[b] - sg_eval(center(b), qp, nullptr);
+            ncost += r * r;
+          }
+          ncost = warp_sum(ncost);
         }
-        ncost = warp_sum(ncost);
       }
       if (ncost < cost) {
         double rel = (cost - ncost) / cost;
         for (int i = 0; i < 4; ++i) p[i] = qp[i];
         cost = ncost;
+        fresh = true;
         lambda /= 10.0;
         if (rel < 1e-15) break;
       } else {

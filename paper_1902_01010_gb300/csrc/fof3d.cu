@@ -13,7 +13,10 @@
 //     every sub-cell, link cell and coarse cell (2^q link cells per axis) one contiguous
 //     run;
 //  3. a dense table over coarse cells gives each link-cell lookup in one load plus a
-//     short binary search;
+//     short binary search; before it, one bit per link cell (the grid folded to 2^m
+//     cells per axis, 8 n bits or more, 4x4x4 cells per 64-bit word) tells most empty
+//     neighbours apart in one cached load: a clear bit means an empty link cell, a set
+//     bit (the cell, or one folded onto it, holds particles) goes on to the lookup;
 //  4. one thread per sub-cell A tests A against the later sub-cells of its own link cell
 //     and all sub-cells of the 13 forward link cells: box distances settle most pairs
 //     (none linked / all linked); the rest are skipped when A and B are already in one
@@ -41,6 +44,7 @@ struct FofGeom {
   int bl;       // bits per axis of link-cell coordinates
   int q;        // coarse cell = 2^q link cells per axis
   int64_t ncoarse;
+  int om;       // occupancy bitmap: link cells folded to 2^om per axis
 };
 
 // Coarse table size: at most 8^m entries with 8^m <= max(n, 4096), m <= 9 (2^27).
@@ -49,6 +53,15 @@ int coarse_bits_per_axis(int64_t n) {
   while (m < 9 && (1LL << (3 * (m + 1))) <= n) ++m;
   return m;
 }
+
+// Occupancy bitmap: 2^(3m) bits, the smallest m >= 4 with 2^(3m) >= 8 n, m <= 11.
+int occ_bits_per_axis(int64_t n) {
+  int m = 4;
+  while (m < 11 && (1LL << (3 * m)) < 8 * n) ++m;
+  return m;
+}
+
+int64_t occ_words(int om) { return 1LL << (3 * om - 6); }
 
 int64_t isqrt64(int64_t x) {
   int64_t r = (int64_t)sqrt((double)x);
@@ -68,6 +81,7 @@ FofGeom fof_geom(int64_t link_d2, int64_t n) {
   int m = coarse_bits_per_axis(n);
   g.q = g.bl - m > 0 ? g.bl - m : 0;
   g.ncoarse = 1LL << (3 * (g.bl - g.q));
+  g.om = occ_bits_per_axis(n);
   return g;
 }
 
@@ -80,10 +94,11 @@ struct FofBufs {
   uint32_t *head;     // 1 at the first particle of each sub-cell, then its exclusive scan
   uint32_t *sc_start; // first sorted index of each sub-cell
   uint32_t *cstart, *cend;
+  unsigned long long *occ;  // occupancy bitmap of the link cells
   void *scratch;      // radix sort / scan scratch
 };
 
-FofBufs fof_carve(Arena &ar, int64_t n, int64_t ncoarse) {
+FofBufs fof_carve(Arena &ar, int64_t n, int64_t ncoarse, int om) {
   FofBufs b;
   b.k0 = ar.take<u64>(n);
   b.k1 = ar.take<u64>(n);
@@ -96,6 +111,7 @@ FofBufs fof_carve(Arena &ar, int64_t n, int64_t ncoarse) {
   b.sc_start = ar.take<uint32_t>(n + 1);
   b.cstart = ar.take<uint32_t>(ncoarse);
   b.cend = ar.take<uint32_t>(ncoarse);
+  b.occ = ar.take<unsigned long long>(occ_words(om));
   size_t a = radix_scratch_bytes<u64>(n), c = scan_scratch_bytes<uint32_t>(n + 1);
   b.scratch = ar.take<char>(a > c ? a : c);
   return b;
@@ -106,6 +122,21 @@ __device__ __forceinline__ uint32_t link_of(uint32_t c, int GL) {
   uint32_t l = c >> 1;
   return l < (uint32_t)GL ? l : (uint32_t)GL - 1u;
 }
+
+// Word and bit of link cell (x, y, z) in the occupancy bitmap: coordinates taken modulo
+// 2^om, then 4x4x4 cells per 64-bit word, words in x-fastest order.
+__device__ __forceinline__ void occ_pos(uint32_t x, uint32_t y, uint32_t z, int om, u64 &word,
+                                        uint32_t &bit) {
+  const uint32_t M = (1u << om) - 1u;
+  x &= M;
+  y &= M;
+  z &= M;
+  const int b = om - 2;
+  word = (u64)(x >> 2) | ((u64)(y >> 2) << b) | ((u64)(z >> 2) << (2 * b));
+  bit = (x & 3u) | ((y & 3u) << 2) | ((z & 3u) << 4);
+}
+
+__device__ __forceinline__ uint32_t compact3(u64 x);
 
 // Sort key: Morton code of the link cell << 6 | 2-bit sub-cell position per axis. Link
 // cells (key >> 6) and coarse cells are its prefixes.
@@ -131,7 +162,8 @@ __global__ void k_fof_prepare(const int32_t *__restrict__ pos, const u64 *__rest
                               const uint32_t *__restrict__ orig, int64_t n, int cshift,
                               int4 *__restrict__ posS, int *__restrict__ minidx,
                               uint32_t *__restrict__ head, uint32_t *__restrict__ cstart,
-                              uint32_t *__restrict__ cend) {
+                              uint32_t *__restrict__ cend, unsigned long long *__restrict__ occ,
+                              int om) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p > n) return;
   if (p == n) {
@@ -145,6 +177,12 @@ __global__ void k_fof_prepare(const int32_t *__restrict__ pos, const u64 *__rest
   minidx[p] = 0x7fffffff;
   u64 k = keyS[p];
   head[p] = (p == 0 || keyS[p - 1] != k) ? 1u : 0u;
+  if (p == 0 || (keyS[p - 1] >> 6) != (k >> 6)) {  // first particle of its link cell
+    u64 w;
+    uint32_t bit;
+    occ_pos(compact3(k >> 6), compact3(k >> 7), compact3(k >> 8), om, w, bit);
+    atomicOr(&occ[w], 1ull << bit);
+  }
   u64 c = k >> cshift;
   if (p == 0 || (keyS[p - 1] >> cshift) != c) cstart[c] = (uint32_t)p;
   if (p == n - 1 || (keyS[p + 1] >> cshift) != c) cend[c] = (uint32_t)(p + 1);
@@ -207,7 +245,7 @@ __device__ __forceinline__ int axis_gap(int alo, int ahi, int blo, int bhi, long
   return shift;
 }
 
-__device__ __forceinline__ uint32_t compact3(u64 x) {
+__device__ __forceinline__ uint32_t compact3(u64 x) {  // every third bit of x, from bit 0
   x &= 0x1249249249249249ULL;
   x = (x ^ (x >> 2)) & 0x10c30c30c30c30c3ULL;
   x = (x ^ (x >> 4)) & 0x100f00f00f00f00fULL;
@@ -224,14 +262,30 @@ __device__ __forceinline__ void subcell_of(u64 key, uint32_t *c) {
   c[2] = 2u * compact3(l >> 2) + (uint32_t)(key & 3u);
 }
 
-// Links sub-cell A = [a0, a1) with sub-cell B = [b0, b1) if any pair of their members is
-// within the linking length.
+// Pairs of sub-cells with at most this many member pairs are tested particle by particle,
+// without the box tests.
+constexpr uint32_t kDirectPairs = 4;
+
+// Links sub-cell A = [a0, a1) with sub-cell B = [b0, b1) (sub-cell coordinates bc) if any
+// pair of their members is within the linking length.
 __device__ __forceinline__ void link_subcells(const int4 *__restrict__ posS, int *parent,
                                               uint32_t a0, uint32_t a1, const int *alo,
                                               const int *ahi, uint32_t b0, uint32_t b1,
-                                              u64 bkey, int S, long long T) {
-  uint32_t bc[3];
-  subcell_of(bkey, bc);
+                                              uint32_t bcx, uint32_t bcy, uint32_t bcz, int S,
+                                              long long T) {
+  const uint32_t bc[3] = {bcx, bcy, bcz};
+  if ((a1 - a0) * (b1 - b0) <= kDirectPairs) {
+    for (uint32_t a = a0; a < a1; ++a) {
+      const int4 xa = posS[a];
+      for (uint32_t b = b0; b < b1; ++b) {
+        if (d2_periodic(xa, posS[b]) < T) {
+          uf_unite(parent, (int)a0, (int)b0);
+          return;
+        }
+      }
+    }
+    return;
+  }
   long long mind = 0, maxd = 0;
   int bl[3], bh[3];
 #pragma unroll
@@ -268,15 +322,16 @@ __device__ __forceinline__ void link_subcells(const int4 *__restrict__ posS, int
 
 // One thread per sub-cell A: A against the later sub-cells of its own link cell and
 // every sub-cell of the 13 forward link cells.
-__global__ void __launch_bounds__(256) k_fof_link(const int4 *__restrict__ posS,
+__global__ void __launch_bounds__(256, 6) k_fof_link(const int4 *__restrict__ posS,
                                                   const u64 *__restrict__ keyS,
                                                   const uint32_t *__restrict__ sid,
                                                   const uint32_t *__restrict__ sc_start,
                                                   const uint32_t *__restrict__ nsc_ptr,
                                                   const uint32_t *__restrict__ cstart,
-                                                  const uint32_t *__restrict__ cend, int *parent,
-                                                  int64_t n, int S, int GL, int qshift,
-                                                  long long T) {
+                                                  const uint32_t *__restrict__ cend,
+                                                  const unsigned long long *__restrict__ occ,
+                                                  int om, int *parent, int64_t n, int S, int GL,
+                                                  int qshift, long long T) {
   int64_t A = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (A >= (int64_t)*nsc_ptr) return;
   const uint32_t a0 = sc_start[A], a1 = sc_start[A + 1];
@@ -287,22 +342,30 @@ __global__ void __launch_bounds__(256) k_fof_link(const int4 *__restrict__ posS,
 #pragma unroll
   for (int k = 0; k < 3; ++k) cell_span((int)ac[k], S, alo[k], ahi[k]);
   const u64 lkey = akey >> 6;
+  const int fx = (int)compact3(lkey), fy = (int)compact3(lkey >> 1), fz = (int)compact3(lkey >> 2);
+  // sub-cell coordinates of a key in link cell (lx, ly, lz): 2 l + the key's 2-bit position
+#define VR_SUB_OF(bk, lx, ly, lz)                                       \
+  2u * (uint32_t)(lx) + (uint32_t)(((bk) >> 4) & 3u),                   \
+      2u * (uint32_t)(ly) + (uint32_t)(((bk) >> 2) & 3u),               \
+      2u * (uint32_t)(lz) + (uint32_t)((bk) & 3u)
   // later sub-cells of the own link cell
   for (uint32_t j = a1; j < (uint32_t)n;) {
     const u64 bk = keyS[j];
     if ((bk >> 6) != lkey) break;
     uint32_t j1 = sc_start[sid[j] + 1];
-    link_subcells(posS, parent, a0, a1, alo, ahi, j, j1, bk, S, T);
+    link_subcells(posS, parent, a0, a1, alo, ahi, j, j1, VR_SUB_OF(bk, fx, fy, fz), S, T);
     j = j1;
   }
-  const u64 lk = akey >> 6;
-  const int fx = (int)compact3(lk), fy = (int)compact3(lk >> 1), fz = (int)compact3(lk >> 2);
 #pragma unroll 1
   for (int s = 0; s < 13; ++s) {
     int nx = fx + c_fwd[s][0], ny = fy + c_fwd[s][1], nz = fz + c_fwd[s][2];
     nx = nx < 0 ? nx + GL : (nx >= GL ? nx - GL : nx);
     ny = ny < 0 ? ny + GL : (ny >= GL ? ny - GL : ny);
     nz = nz < 0 ? nz + GL : (nz >= GL ? nz - GL : nz);
+    u64 ow;
+    uint32_t ob;
+    occ_pos((uint32_t)nx, (uint32_t)ny, (uint32_t)nz, om, ow, ob);
+    if (!((__ldg(&occ[ow]) >> ob) & 1ull)) continue;  // empty link cell
     u64 key = morton3((uint32_t)nx, (uint32_t)ny, (uint32_t)nz);  // link-cell key
     u64 c = key >> qshift;                                        // its coarse cell
     uint32_t lo = __ldg(&cstart[c]);
@@ -316,7 +379,7 @@ __global__ void __launch_bounds__(256) k_fof_link(const int4 *__restrict__ posS,
       const u64 bk = keyS[j];
       if ((bk >> 6) != key) break;
       uint32_t j1 = sc_start[sid[j] + 1];
-      link_subcells(posS, parent, a0, a1, alo, ahi, j, j1, bk, S, T);
+      link_subcells(posS, parent, a0, a1, alo, ahi, j, j1, VR_SUB_OF(bk, nx, ny, nz), S, T);
       j = j1;
     }
   }
@@ -344,7 +407,7 @@ __global__ void k_fof_label(int *parent, const int4 *__restrict__ posS,
 
 size_t ws_fof3d(int64_t n) {
   Arena ar;
-  fof_carve(ar, n, 1LL << (3 * coarse_bits_per_axis(n)));
+  fof_carve(ar, n, 1LL << (3 * coarse_bits_per_axis(n)), occ_bits_per_axis(n));
   return ar.off;
 }
 
@@ -364,7 +427,7 @@ extern "C" vr_status vr_fof3d(vr_ctx *ctx, const int32_t *pos, int64_t n, int64_
   cudaStream_t s = (cudaStream_t)stream;
   FofGeom g = fof_geom(link_d2, n);
   Arena ar(ws, ws_bytes);
-  FofBufs B = fof_carve(ar, n, g.ncoarse);
+  FofBufs B = fof_carve(ar, n, g.ncoarse, g.om);
   vr_status st = check_ws(ctx, ar, ws_bytes);
   if (st != VR_OK) return st;
   const int T = 256;
@@ -376,10 +439,11 @@ extern "C" vr_status vr_fof3d(vr_ctx *ctx, const int32_t *pos, int64_t n, int64_
   u64 *keyS = which ? B.k1 : B.k0;
   uint32_t *orig = which ? B.v1 : B.v0;
   VR_CUDA(ctx, cudaMemsetAsync(B.cstart, 0xff, g.ncoarse * sizeof(uint32_t), s));
+  VR_CUDA(ctx, cudaMemsetAsync(B.occ, 0, occ_words(g.om) * sizeof(unsigned long long), s));
   const int qshift = 3 * g.q;      // link-cell key -> coarse-cell key
   const int cshift = 6 + qshift;   // sort key -> coarse-cell key
   k_fof_prepare<<<grid_for(n + 1, T), T, 0, s>>>(pos, keyS, orig, n, cshift, B.posS, B.minidx,
-                                                 B.head, B.cstart, B.cend);
+                                                 B.head, B.cstart, B.cend, B.occ, g.om);
   VR_LAUNCHED(ctx, "k_fof_prepare");
   VR_CUDA(ctx, exclusive_scan<uint32_t>(B.head, B.head, n + 1, B.scratch, s));
   uint32_t *sid = which ? B.v0 : B.v1;  // the sort's spare value buffer
@@ -389,7 +453,7 @@ extern "C" vr_status vr_fof3d(vr_ctx *ctx, const int32_t *pos, int64_t n, int64_
   VR_LAUNCHED(ctx, "k_fof_hook");
   // the number of sub-cells, head[n], stays on the device; threads beyond it idle
   VR_TIMED(ctx, "fof_link", s, k_fof_link<<<grid_for(n, T), T, 0, s>>>(B.posS, keyS, sid, B.sc_start, B.head + n, B.cstart,
-                                          B.cend, B.parent, n, g.S, g.GL, qshift,
+                                          B.cend, B.occ, g.om, B.parent, n, g.S, g.GL, qshift,
                                           (long long)link_d2));
   VR_LAUNCHED(ctx, "k_fof_link");
   k_fof_roots<<<grid_for(n, T), T, 0, s>>>(B.parent, B.posS, n, B.minidx);
