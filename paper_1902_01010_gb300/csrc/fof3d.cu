@@ -17,10 +17,16 @@
 //     cells per axis, 8 n bits or more, 4x4x4 cells per 64-bit word) tells most empty
 //     neighbours apart in one cached load: a clear bit means an empty link cell, a set
 //     bit (the cell, or one folded onto it, holds particles) goes on to the lookup;
-//  4. one thread per sub-cell A tests A against the later sub-cells of its own link cell
-//     and all sub-cells of the 13 forward link cells: box distances settle most pairs
-//     (none linked / all linked); the rest are skipped when A and B are already in one
-//     component, otherwise particles are tested until a linked pair is found. Linked
+//  4. link cells are listed as runs of sub-cells; a warp takes 32 consecutive link cells,
+//     each lane screening one against the bitmap of its 13 forward neighbours. A lane
+//     whose link cell is one sub-cell links it on its own (a lookup and the sub-cell
+//     pairs per occupied neighbour); a link cell of several sub-cells is taken by the
+//     whole warp: lanes 0-12 find the 13 neighbours at once, the neighbour sub-cells are
+//     gathered in shared memory, and the (own, neighbour) and (own, own) sub-cell pairs
+//     are spread over the lanes. A pair of sub-cells with at most 4 member pairs is
+//     tested particle by particle; otherwise box distances settle most pairs (none
+//     linked / all linked), the rest are skipped when A and B are already in one
+//     component, else particles are tested until a linked pair is found. Linked
 //     sub-cells are merged by a lock-free union-find (atomicCAS hooks the larger root
 //     under the smaller; finds halve paths);
 //  5. labels are the minimum original index of each component (atomicMin per root).
@@ -100,8 +106,8 @@ struct FofBufs {
 
 FofBufs fof_carve(Arena &ar, int64_t n, int64_t ncoarse, int om) {
   FofBufs b;
-  b.k0 = ar.take<u64>(n);
-  b.k1 = ar.take<u64>(n);
+  b.k0 = ar.take<u64>(n + 1);  // n + 1: the spare one holds 2 n + 2 link-cell words
+  b.k1 = ar.take<u64>(n + 1);
   b.v0 = ar.take<uint32_t>(n);
   b.v1 = ar.take<uint32_t>(n);
   b.posS = ar.take<int4>(n);
@@ -155,8 +161,6 @@ __global__ void k_fof_keys(const int32_t *__restrict__ pos, int64_t n, int S, in
   vals[i] = (uint32_t)i;
 }
 
-// Sub-cell coordinates of a sort key.
-__device__ __forceinline__ void subcell_of(u64 key, uint32_t *c);
 
 __global__ void k_fof_prepare(const int32_t *__restrict__ pos, const u64 *__restrict__ keyS,
                               const uint32_t *__restrict__ orig, int64_t n, int cshift,
@@ -255,12 +259,6 @@ __device__ __forceinline__ uint32_t compact3(u64 x) {  // every third bit of x, 
   return (uint32_t)x;
 }
 
-__device__ __forceinline__ void subcell_of(u64 key, uint32_t *c) {
-  const u64 l = key >> 6;
-  c[0] = 2u * compact3(l) + (uint32_t)((key >> 4) & 3u);
-  c[1] = 2u * compact3(l >> 1) + (uint32_t)((key >> 2) & 3u);
-  c[2] = 2u * compact3(l >> 2) + (uint32_t)(key & 3u);
-}
 
 // Pairs of sub-cells with at most this many member pairs are tested particle by particle,
 // without the box tests.
@@ -320,67 +318,217 @@ __device__ __forceinline__ void link_subcells(const int4 *__restrict__ posS, int
   }
 }
 
-// One thread per sub-cell A: A against the later sub-cells of its own link cell and
-// every sub-cell of the 13 forward link cells.
-__global__ void __launch_bounds__(256, 6) k_fof_link(const int4 *__restrict__ posS,
-                                                  const u64 *__restrict__ keyS,
-                                                  const uint32_t *__restrict__ sid,
-                                                  const uint32_t *__restrict__ sc_start,
-                                                  const uint32_t *__restrict__ nsc_ptr,
-                                                  const uint32_t *__restrict__ cstart,
-                                                  const uint32_t *__restrict__ cend,
-                                                  const unsigned long long *__restrict__ occ,
-                                                  int om, int *parent, int64_t n, int S, int GL,
-                                                  int qshift, long long T) {
-  int64_t A = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (A >= (int64_t)*nsc_ptr) return;
-  const uint32_t a0 = sc_start[A], a1 = sc_start[A + 1];
-  const u64 akey = keyS[a0];
-  int alo[3], ahi[3];
-  uint32_t ac[3];
-  subcell_of(akey, ac);
-#pragma unroll
-  for (int k = 0; k < 3; ++k) cell_span((int)ac[k], S, alo[k], ahi[k]);
-  const u64 lkey = akey >> 6;
-  const int fx = (int)compact3(lkey), fy = (int)compact3(lkey >> 1), fz = (int)compact3(lkey >> 2);
-  // sub-cell coordinates of a key in link cell (lx, ly, lz): 2 l + the key's 2-bit position
+// Sub-cell coordinates of sort key bk in link cell (lx, ly, lz): 2 l + the key's 2-bit
+// position along each axis (three comma-separated values).
 #define VR_SUB_OF(bk, lx, ly, lz)                                       \
   2u * (uint32_t)(lx) + (uint32_t)(((bk) >> 4) & 3u),                   \
       2u * (uint32_t)(ly) + (uint32_t)(((bk) >> 2) & 3u),               \
       2u * (uint32_t)(lz) + (uint32_t)((bk) & 3u)
-  // later sub-cells of the own link cell
-  for (uint32_t j = a1; j < (uint32_t)n;) {
-    const u64 bk = keyS[j];
-    if ((bk >> 6) != lkey) break;
-    uint32_t j1 = sc_start[sid[j] + 1];
-    link_subcells(posS, parent, a0, a1, alo, ahi, j, j1, VR_SUB_OF(bk, fx, fy, fz), S, T);
-    j = j1;
+
+// Link cells as runs of sub-cells: flag[A] = 1 at the first sub-cell A of each link cell
+// (entries [0, n]; zero from nsc on), scanned in place into link-cell ids.
+__global__ void k_fof_lcflags(const u64 *__restrict__ keyS, const uint32_t *__restrict__ sc_start,
+                              const uint32_t *__restrict__ nsc_ptr, int64_t n,
+                              uint32_t *__restrict__ flag) {
+  const int64_t A = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (A > n) return;
+  const int64_t nsc = *nsc_ptr;
+  uint32_t f = 0;
+  if (A < nsc)
+    f = (A == 0 || (keyS[sc_start[A - 1]] >> 6) != (keyS[sc_start[A]] >> 6)) ? 1u : 0u;
+  flag[A] = f;
+}
+
+// After the scan (lcf[A] = link cell of a first sub-cell A, lcf[n] = number of link
+// cells): lcfirst[c] = first sub-cell of link cell c, lcfirst[nlc] = nsc.
+__global__ void k_fof_lcfirst(const u64 *__restrict__ keyS, const uint32_t *__restrict__ sc_start,
+                              const uint32_t *__restrict__ nsc_ptr, int64_t n,
+                              const uint32_t *__restrict__ lcf, uint32_t *__restrict__ lcfirst) {
+  const int64_t A = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (A > n) return;
+  const int64_t nsc = *nsc_ptr;
+  if (A > nsc) return;
+  if (A == nsc) {
+    lcfirst[lcf[A]] = (uint32_t)nsc;
+    return;
   }
+  if (A == 0 || (keyS[sc_start[A - 1]] >> 6) != (keyS[sc_start[A]] >> 6))
+    lcfirst[lcf[A]] = (uint32_t)A;
+}
+
+constexpr int kLW = 8;       // warps per block of the link-cell kernel
+constexpr int kLCap = 128;   // neighbour sub-cells a warp holds per round
+constexpr int kLMaxSub = 64; // sub-cells of one link cell (4 x 4 x 4 at most)
+
+__device__ __forceinline__ u64 pack_sub(uint32_t x, uint32_t y, uint32_t z) {
+  return (u64)x | ((u64)y << 21) | ((u64)z << 42);
+}
+
+// Sub-cell pair (A, B) from packed sub-cell coordinates.
+__device__ __forceinline__ void link_pair(const int4 *__restrict__ posS, int *parent, uint32_t a0,
+                                          uint32_t a1, u64 ac, uint32_t b0, uint32_t b1, u64 bc,
+                                          int S, long long T) {
+  const u64 M = (1ull << 21) - 1ull;
+  int alo[3], ahi[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) cell_span((int)((ac >> (21 * k)) & M), S, alo[k], ahi[k]);
+  link_subcells(posS, parent, a0, a1, alo, ahi, b0, b1, (uint32_t)(bc & M),
+                (uint32_t)((bc >> 21) & M), (uint32_t)(bc >> 42), S, T);
+}
+
+// Persistent grid; each warp takes 32 consecutive link cells (sort order) at a time. Lane l
+// screens link cell c0 + l against the occupancy bitmap of its 13 forward neighbours; a
+// single-sub-cell link cell with occupied neighbours is linked by its lane alone; a link
+// cell of several sub-cells is linked by the whole warp: the pairs of its own sub-cells,
+// then, with lanes 0-12 each finding one forward link cell, every (own sub-cell,
+// neighbour sub-cell) pair, the pairs spread over the lanes. Neighbour sub-cells are
+// gathered kLCap at a time.
+__global__ void __launch_bounds__(32 * kLW, 5) k_fof_link_w(
+    const int4 *__restrict__ posS, const u64 *__restrict__ keyS, const uint32_t *__restrict__ sid,
+    const uint32_t *__restrict__ sc_start, const uint32_t *__restrict__ lcf,
+    const uint32_t *__restrict__ lcfirst, const uint32_t *__restrict__ cstart,
+    const uint32_t *__restrict__ cend, const unsigned long long *__restrict__ occ, int om,
+    int *parent, int64_t n, int S, int GL, int qshift, long long T) {
+  __shared__ uint32_t s_b0[kLW][kLCap], s_b1[kLW][kLCap];
+  __shared__ u64 s_bc[kLW][kLCap];
+  __shared__ uint32_t s_a0[kLW][kLMaxSub + 1];
+  __shared__ u64 s_ac[kLW][kLMaxSub];
+  __shared__ int s_cnt[kLW];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned FULL = 0xffffffffu;
+  const int64_t nlc = lcf[n];
+  for (int64_t c0 = ((int64_t)blockIdx.x * kLW + w) * 32; c0 < nlc; c0 += (int64_t)gridDim.x * kLW * 32) {
+    // lane l screens link cell c0 + l: one sub-cell and no forward neighbour in the
+    // occupancy bitmap means nothing to link
+    int my_m = 0, mfx = 0, mfy = 0, mfz = 0;
+    uint32_t my_s0 = 0, my_bits = 0;
+    if (c0 + lane < nlc) {
+      my_s0 = lcfirst[c0 + lane];
+      my_m = (int)(lcfirst[c0 + lane + 1] - my_s0);
+      const u64 k = keyS[sc_start[my_s0]] >> 6;
+      mfx = (int)compact3(k);
+      mfy = (int)compact3(k >> 1);
+      mfz = (int)compact3(k >> 2);
 #pragma unroll 1
-  for (int s = 0; s < 13; ++s) {
-    int nx = fx + c_fwd[s][0], ny = fy + c_fwd[s][1], nz = fz + c_fwd[s][2];
-    nx = nx < 0 ? nx + GL : (nx >= GL ? nx - GL : nx);
-    ny = ny < 0 ? ny + GL : (ny >= GL ? ny - GL : ny);
-    nz = nz < 0 ? nz + GL : (nz >= GL ? nz - GL : nz);
-    u64 ow;
-    uint32_t ob;
-    occ_pos((uint32_t)nx, (uint32_t)ny, (uint32_t)nz, om, ow, ob);
-    if (!((__ldg(&occ[ow]) >> ob) & 1ull)) continue;  // empty link cell
-    u64 key = morton3((uint32_t)nx, (uint32_t)ny, (uint32_t)nz);  // link-cell key
-    u64 c = key >> qshift;                                        // its coarse cell
-    uint32_t lo = __ldg(&cstart[c]);
-    if (lo == kEmpty) continue;
-    uint32_t hi = __ldg(&cend[c]);
-    while (lo < hi) {
-      uint32_t mid = (lo + hi) >> 1;
-      if ((keyS[mid] >> 6) < key) lo = mid + 1; else hi = mid;
+      for (int q = 0; q < 13; ++q) {
+        int x = mfx + c_fwd[q][0], y = mfy + c_fwd[q][1], z = mfz + c_fwd[q][2];
+        x = x < 0 ? x + GL : (x >= GL ? x - GL : x);
+        y = y < 0 ? y + GL : (y >= GL ? y - GL : y);
+        z = z < 0 ? z + GL : (z >= GL ? z - GL : z);
+        u64 ow;
+        uint32_t ob;
+        occ_pos((uint32_t)x, (uint32_t)y, (uint32_t)z, om, ow, ob);
+        if ((__ldg(&occ[ow]) >> ob) & 1ull) my_bits |= 1u << q;
+      }
     }
-    for (uint32_t j = lo; j < (uint32_t)n;) {
-      const u64 bk = keyS[j];
-      if ((bk >> 6) != key) break;
-      uint32_t j1 = sc_start[sid[j] + 1];
-      link_subcells(posS, parent, a0, a1, alo, ahi, j, j1, VR_SUB_OF(bk, nx, ny, nz), S, T);
-      j = j1;
+    if (my_m == 1 && my_bits != 0) {  // a single sub-cell: this lane links it on its own
+      const uint32_t a0 = sc_start[my_s0], a1 = sc_start[my_s0 + 1];
+      const u64 ak = keyS[a0];
+      int alo[3], ahi[3];
+      cell_span((int)(2u * (uint32_t)mfx + (uint32_t)((ak >> 4) & 3u)), S, alo[0], ahi[0]);
+      cell_span((int)(2u * (uint32_t)mfy + (uint32_t)((ak >> 2) & 3u)), S, alo[1], ahi[1]);
+      cell_span((int)(2u * (uint32_t)mfz + (uint32_t)(ak & 3u)), S, alo[2], ahi[2]);
+#pragma unroll 1
+      for (int q = 0; q < 13; ++q) {
+        if (!((my_bits >> q) & 1u)) continue;
+        int x = mfx + c_fwd[q][0], y = mfy + c_fwd[q][1], z = mfz + c_fwd[q][2];
+        x = x < 0 ? x + GL : (x >= GL ? x - GL : x);
+        y = y < 0 ? y + GL : (y >= GL ? y - GL : y);
+        z = z < 0 ? z + GL : (z >= GL ? z - GL : z);
+        const u64 key = morton3((uint32_t)x, (uint32_t)y, (uint32_t)z);
+        const u64 c = key >> qshift;
+        uint32_t lo = __ldg(&cstart[c]);
+        if (lo == kEmpty) continue;
+        uint32_t hi = __ldg(&cend[c]);
+        while (lo < hi) {
+          const uint32_t mid = (lo + hi) >> 1;
+          if ((keyS[mid] >> 6) < key) lo = mid + 1; else hi = mid;
+        }
+        for (uint32_t j = lo; j < (uint32_t)n;) {
+          const u64 bk = keyS[j];
+          if ((bk >> 6) != key) break;
+          const uint32_t j1 = sc_start[sid[j] + 1];
+          link_subcells(posS, parent, a0, a1, alo, ahi, j, j1, VR_SUB_OF(bk, x, y, z), S, T);
+          j = j1;
+        }
+      }
+      my_bits = 0;
+    }
+    unsigned todo = __ballot_sync(FULL, my_m > 1 || my_bits != 0);
+    while (todo) {
+    const int src = __ffs(todo) - 1;
+    todo &= todo - 1;
+    const uint32_t s0 = __shfl_sync(FULL, my_s0, src);
+    const int m = __shfl_sync(FULL, my_m, src);
+    const int fx = __shfl_sync(FULL, mfx, src), fy = __shfl_sync(FULL, mfy, src),
+              fz = __shfl_sync(FULL, mfz, src);
+    const uint32_t bits = __shfl_sync(FULL, my_bits, src);
+    for (int i = lane; i <= m; i += 32) {  // sub-cell starts (and the end of the last)
+      const uint32_t p0 = sc_start[s0 + i];
+      s_a0[w][i] = p0;
+      if (i < m) {
+        const u64 k = keyS[p0];
+        s_ac[w][i] = pack_sub(VR_SUB_OF(k, fx, fy, fz));
+      }
+    }
+    __syncwarp();
+    for (int t = lane; t < m * m; t += 32) {  // own sub-cells, i < j
+      const int i = t / m, j = t - i * m;
+      if (j <= i) continue;
+      link_pair(posS, parent, s_a0[w][i], s_a0[w][i + 1], s_ac[w][i], s_a0[w][j], s_a0[w][j + 1],
+                s_ac[w][j], S, T);
+    }
+    uint32_t cur = (uint32_t)n;  // lane k < 13: next particle of forward link cell k
+    u64 nkey = 0;
+    int nx = 0, ny = 0, nz = 0;
+    if (lane < 13 && ((bits >> lane) & 1u)) {
+      nx = fx + c_fwd[lane][0];
+      ny = fy + c_fwd[lane][1];
+      nz = fz + c_fwd[lane][2];
+      nx = nx < 0 ? nx + GL : (nx >= GL ? nx - GL : nx);
+      ny = ny < 0 ? ny + GL : (ny >= GL ? ny - GL : ny);
+      nz = nz < 0 ? nz + GL : (nz >= GL ? nz - GL : nz);
+      {
+        nkey = morton3((uint32_t)nx, (uint32_t)ny, (uint32_t)nz);
+        const u64 c = nkey >> qshift;
+        uint32_t lo = __ldg(&cstart[c]);
+        if (lo != kEmpty) {
+          uint32_t hi = __ldg(&cend[c]);
+          while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if ((keyS[mid] >> 6) < nkey) lo = mid + 1; else hi = mid;
+          }
+          cur = lo;
+        }
+      }
+    }
+    while (__any_sync(FULL, cur < (uint32_t)n)) {
+      if (lane == 0) s_cnt[w] = 0;
+      __syncwarp();
+      while (cur < (uint32_t)n) {
+        const u64 bk = keyS[cur];
+        if ((bk >> 6) != nkey) {
+          cur = (uint32_t)n;
+          break;
+        }
+        const int slot = atomicAdd(&s_cnt[w], 1);
+        if (slot >= kLCap) break;  // full: this sub-cell waits for the next round
+        const uint32_t j1 = sc_start[sid[cur] + 1];
+        s_b0[w][slot] = cur;
+        s_b1[w][slot] = j1;
+        s_bc[w][slot] = pack_sub(VR_SUB_OF(bk, nx, ny, nz));
+        cur = j1;
+      }
+      __syncwarp();
+      const int nb = min(s_cnt[w], kLCap);
+      for (int t = lane; t < m * nb; t += 32) {
+        const int i = t / nb, j = t - i * nb;
+        link_pair(posS, parent, s_a0[w][i], s_a0[w][i + 1], s_ac[w][i], s_b0[w][j], s_b1[w][j],
+                  s_bc[w][j], S, T);
+      }
+      __syncwarp();
+    }
+    __syncwarp();  // s_a0 / s_ac are rewritten for the next link cell
     }
   }
 }
@@ -451,11 +599,22 @@ extern "C" vr_status vr_fof3d(vr_ctx *ctx, const int32_t *pos, int64_t n, int64_
   VR_LAUNCHED(ctx, "k_fof_subcells");
   k_fof_hook<<<grid_for(n, T), T, 0, s>>>(sid, B.sc_start, n, B.parent);
   VR_LAUNCHED(ctx, "k_fof_hook");
-  // the number of sub-cells, head[n], stays on the device; threads beyond it idle
-  VR_TIMED(ctx, "fof_link", s, k_fof_link<<<grid_for(n, T), T, 0, s>>>(B.posS, keyS, sid, B.sc_start, B.head + n, B.cstart,
+  // link cells as runs of sub-cells, in the sort's spare key buffer (2 n + 2 words):
+  // lcf [0, n] the scanned first-sub-cell flags, lcfirst [n + 1, 2 n + 2) the first
+  // sub-cell of each link cell; the number of sub-cells, head[n], stays on the device
+  uint32_t *lcf = reinterpret_cast<uint32_t *>(which ? B.k0 : B.k1);
+  uint32_t *lcfirst = lcf + (n + 1);
+  k_fof_lcflags<<<grid_for(n + 1, T), T, 0, s>>>(keyS, B.sc_start, B.head + n, n, lcf);
+  VR_LAUNCHED(ctx, "k_fof_lcflags");
+  VR_CUDA(ctx, exclusive_scan<uint32_t>(lcf, lcf, n + 1, B.scratch, s));
+  k_fof_lcfirst<<<grid_for(n + 1, T), T, 0, s>>>(keyS, B.sc_start, B.head + n, n, lcf, lcfirst);
+  VR_LAUNCHED(ctx, "k_fof_lcfirst");
+  int sms = ctx->sm_count;
+  if (sms <= 0) VR_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+  VR_TIMED(ctx, "fof_link", s, k_fof_link_w<<<5 * sms, 32 * kLW, 0, s>>>(B.posS, keyS, sid, B.sc_start, lcf, lcfirst, B.cstart,
                                           B.cend, B.occ, g.om, B.parent, n, g.S, g.GL, qshift,
                                           (long long)link_d2));
-  VR_LAUNCHED(ctx, "k_fof_link");
+  VR_LAUNCHED(ctx, "k_fof_link_w");
   k_fof_roots<<<grid_for(n, T), T, 0, s>>>(B.parent, B.posS, n, B.minidx);
   VR_LAUNCHED(ctx, "k_fof_roots");
   k_fof_label<<<grid_for(n, T), T, 0, s>>>(B.parent, B.posS, B.minidx, n, label);

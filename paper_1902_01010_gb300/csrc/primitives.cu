@@ -140,46 +140,79 @@ __global__ void __launch_bounds__(kRadThreads) k_radix_hist(const K *keys, int64
   counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
+// Stable scatter of one tile: every key's rank inside the tile (by digit, then tile order)
+// is found round by round (kRadThreads keys per round: per-warp peer matching, then a
+// prefix over the warps), the tile is reordered by digit in shared memory, and each
+// digit's run is written out with consecutive threads on consecutive addresses.
 template <class K>
 __global__ void __launch_bounds__(kRadThreads) k_radix_scatter(const K *kin, const uint32_t *vin,
                                                                 K *kout, uint32_t *vout, int64_t n,
                                                                 int shift, int64_t ntiles,
                                                                 const uint32_t *offs) {
-  __shared__ uint32_t s_base[256];     // global output offset of each digit for this tile
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  K *s_key = reinterpret_cast<K *>(s_dyn);                                  // [kRadTile]
+  uint32_t *s_val = reinterpret_cast<uint32_t *>(s_dyn + kRadTile * sizeof(K));  // [kRadTile]
+  __shared__ uint32_t s_base[256];  // global offset of each digit's run of this tile
+  __shared__ uint32_t s_loc[256];   // start of each digit's run inside the tile
+  __shared__ uint32_t s_run[256];   // keys of each digit placed so far
   __shared__ uint32_t s_wcnt[kRadWarps][256];
+  __shared__ uint32_t s_tot[kRadWarps];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  s_base[t] = offs[(int64_t)t * ntiles + blockIdx.x];
-  int64_t base = (int64_t)blockIdx.x * kRadTile;
+  const int64_t base = (int64_t)blockIdx.x * kRadTile;
+  const int tn = (int)min((int64_t)kRadTile, n - base);
+  // this tile's count of digit t: the next entry of the digit-major, tile-minor scan
+  const int64_t ix = (int64_t)t * ntiles + blockIdx.x;
+  const uint32_t off = offs[ix];
+  const uint32_t cnt = (ix + 1 < 256 * ntiles ? offs[ix + 1] : (uint32_t)n) - off;
+  s_base[t] = off;
+  s_run[t] = 0;
+  // exclusive prefix of the counts over the 256 digits
+  uint32_t incl = cnt;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t x = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += x;
+  }
+  if (lane == 31) s_tot[w] = incl;
+  __syncthreads();
+  uint32_t pre = 0;
+  for (int q = 0; q < w; ++q) pre += s_tot[q];
+  s_loc[t] = pre + incl - cnt;
   const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll 1
   for (int r = 0; r < kRadItems; ++r) {
     for (int q = 0; q < kRadWarps; ++q) s_wcnt[q][t] = 0;
     __syncthreads();
-    int64_t i = base + r * kRadThreads + t;
-    bool valid = i < n;
-    K key = valid ? kin[i] : K(0);
-    uint32_t val = valid ? vin[i] : 0u;
-    uint32_t d = valid ? (uint32_t)(key >> shift) & 0xffu : 256u + lane;
-    uint32_t peers = __match_any_sync(0xffffffffu, d);
-    uint32_t rank = __popc(peers & lt);
+    const int li = r * kRadThreads + t;
+    const bool valid = li < tn;
+    const K key = valid ? kin[base + li] : K(0);
+    const uint32_t val = valid ? vin[base + li] : 0u;
+    const uint32_t d = valid ? (uint32_t)(key >> shift) & 0xffu : 256u + lane;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t rank = __popc(peers & lt);
     if (valid && rank == 0) s_wcnt[w][d] = __popc(peers);
     __syncthreads();
-    // per digit (thread t owns digit t): exclusive prefix over warps
-    uint32_t run = 0;
+    uint32_t run = 0;  // thread t owns digit t: exclusive prefix over the warps
     for (int q = 0; q < kRadWarps; ++q) {
-      uint32_t c = s_wcnt[q][t];
+      const uint32_t c = s_wcnt[q][t];
       s_wcnt[q][t] = run;
       run += c;
     }
     __syncthreads();
     if (valid) {
-      uint32_t pos = s_base[d] + s_wcnt[w][d] + rank;
-      kout[pos] = key;
-      vout[pos] = val;
+      const uint32_t lp = s_loc[d] + s_run[d] + s_wcnt[w][d] + rank;
+      s_key[lp] = key;
+      s_val[lp] = val;
     }
     __syncthreads();
-    s_base[t] += run;
-    __syncthreads();
+    s_run[t] += run;
+  }
+  __syncthreads();
+  for (int li = t; li < tn; li += kRadThreads) {
+    const K key = s_key[li];
+    const uint32_t d = (uint32_t)(key >> shift) & 0xffu;
+    const uint32_t pos = s_base[d] + (uint32_t)li - s_loc[d];
+    kout[pos] = key;
+    vout[pos] = s_val[li];
   }
 }
 
@@ -198,6 +231,11 @@ cudaError_t radix_sort_pairs(K *k0, uint32_t *v0, K *k1, uint32_t *v1, int64_t n
   *which = 0;
   if (n <= 1 || end_bit <= begin_bit) return cudaSuccess;
   int64_t ntiles = ceil_div(n, kRadTile);
+  {  // the tile buffers exceed the default 48 KB of shared memory for 64-bit keys
+    cudaError_t e = cudaFuncSetAttribute(k_radix_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(kRadTile * (sizeof(K) + 4)));
+    if (e != cudaSuccess) return e;
+  }
   uint32_t *counts = (uint32_t *)scratch;
   char *scan_scr = (char *)scratch + ((((size_t)ntiles * 256 * sizeof(uint32_t)) + 255) & ~(size_t)255);
   K *kin = k0, *kout = k1;
@@ -210,8 +248,8 @@ cudaError_t radix_sort_pairs(K *k0, uint32_t *v0, K *k1, uint32_t *v1, int64_t n
     if (e != cudaSuccess) return e;
     e = exclusive_scan<uint32_t>(counts, counts, ntiles * 256, scan_scr, s);
     if (e != cudaSuccess) return e;
-    k_radix_scatter<K><<<(unsigned)ntiles, kRadThreads, 0, s>>>(kin, vin, kout, vout, n, shift,
-                                                                ntiles, counts);
+    k_radix_scatter<K><<<(unsigned)ntiles, kRadThreads, kRadTile * (sizeof(K) + 4), s>>>(
+        kin, vin, kout, vout, n, shift, ntiles, counts);
     count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
