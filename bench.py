@@ -328,16 +328,28 @@ def run_ours(args):
         if prelab:
             hl3.copy_(torch.from_numpy(lab_np))
         hl6 = torch.empty(box.n, dtype=torch.int32).pin_memory()
+        # the velocities (needed from the substructure search on) come in on a second
+        # stream while the 3D FOF runs; the 3D labels go out on it during the search
+        cs = torch.cuda.Stream(dev)
         torch.cuda.synchronize(dev)
         t1 = time.perf_counter()
         for _ in range(args.e2e_steps):
             pos.copy_(hpos, non_blocking=True)
-            vel.copy_(hvel, non_blocking=True)
             if prelab:
                 lab.copy_(hl3, non_blocking=True)
-            step()
+            with torch.cuda.stream(cs):
+                vel.copy_(hvel, non_blocking=True)
+                ev_vel = torch.cuda.Event()
+                ev_vel.record(cs)
             if not prelab:
-                hl3.copy_(lab, non_blocking=True)
+                ctx.fof3d(pos, box.link_d2, label=lab)
+                ev_lab = torch.cuda.Event()
+                ev_lab.record(stream)
+                with torch.cuda.stream(cs):
+                    cs.wait_event(ev_lab)
+                    hl3.copy_(lab, non_blocking=True)
+            stream.wait_event(ev_vel)
+            ctx.find_substructure(pos, vel, lab, box.lx_sub, 1.0, P, batched=batched, out=out)
             hl6.copy_(out["label6"], non_blocking=True)
             torch.cuda.synchronize(dev)
         dt = (time.perf_counter() - t1) / args.e2e_steps

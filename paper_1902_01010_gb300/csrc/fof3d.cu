@@ -533,13 +533,23 @@ __global__ void __launch_bounds__(32 * kLW, 5) k_fof_link_w(
   }
 }
 
+// Root of every particle and the minimum original index per root. Neighbours in sort
+// order mostly share a root, so the lanes of a warp with the same root combine their
+// minimum first and one of them updates the root (one atomic per root and warp).
 __global__ void k_fof_roots(int *parent, const int4 *__restrict__ posS, int64_t n,
                             int *__restrict__ minidx) {
-  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= n) return;
-  int r = uf_find(parent, (int)p);
-  parent[p] = r;
-  atomicMin(&minidx[r], posS[p].w);
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const bool valid = p < n;
+  int r = -1 - lane, w = 0x7fffffff;
+  if (valid) {
+    r = uf_find(parent, (int)p);
+    parent[p] = r;
+    w = posS[p].w;
+  }
+  const unsigned peers = __match_any_sync(0xffffffffu, r);
+  const int m = __reduce_min_sync(peers, w);
+  if (valid && lane == __ffs(peers) - 1) atomicMin(&minidx[r], m);
 }
 
 // A fresh find: parent[p] written by k_fof_roots may since have been overwritten by a

@@ -12,14 +12,21 @@ constexpr uint32_t kMaxHalo = 1u << 22;
 
 __global__ void k_count(const int32_t *__restrict__ label, int64_t n, uint32_t *__restrict__ cnt,
                         DevStatus *st) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int32_t l = label[i];
-  if (l < 0 || l >= n) {
-    raise_error(st, VR_ERR_INVALID_ARG, 4);
-    return;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  int32_t l = -1;
+  if (i < n) {
+    l = label[i];
+    if (l < 0 || l >= n) {
+      raise_error(st, VR_ERR_INVALID_ARG, 4);
+      l = -1;
+    }
   }
-  atomicAdd(&cnt[l], 1u);
+  // lanes with the same label add their count once (members of a group are often
+  // neighbours in index order)
+  const int32_t key = l >= 0 ? l : -1 - lane;
+  const unsigned peers = __match_any_sync(0xffffffffu, key);
+  if (l >= 0 && lane == __ffs(peers) - 1) atomicAdd(&cnt[l], (uint32_t)__popc(peers));
 }
 
 // flag[l] = 1 if label l heads a halo; halos larger than 2^22 are rejected.
