@@ -354,11 +354,9 @@ vr_status vr_clean_groups(vr_ctx *ctx, const float *ell, int64_t n, const vr_par
  * the library holds until the process exits.
  *   pos, n, link_d2, label: as for vr_fof3d, with n <= VR_FOF3D_NOALLOC_MAX_N
  *   stream: cudaStream_t on the current device (NULL = legacy default stream)
- * Works on the calling thread's current device. The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) and keeps it for the process; make that
- * first call before any stream capture. cudaDeviceReset on that device unloads the array
- * with the library's module, so the kept address is then stale: do not call this entry
- * point on a device again after resetting it in the same process. All calls share the one array and every call overwrites it: calls whose
+ * Works on the calling thread's current device. Every call looks up the array's device
+ * address in the current context (cudaGetSymbolAddress, which allocates nothing), so
+ * calls after a cudaDeviceReset find the reloaded array. All calls share the one array and every call overwrites it: calls whose
  * work overlaps on the GPU (other streams, or host threads on the same device) race and
  * must be serialised by the caller. Returns VR_ERR_INVALID_ARG for n above the maximum
  * or bad arguments, VR_ERR_CUDA if the address lookup or a launch fails; the status code

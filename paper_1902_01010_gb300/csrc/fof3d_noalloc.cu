@@ -2,8 +2,6 @@
 // the same labels as vr_fof3d, with the scratch taken from one static device array of
 // fixed size instead of a caller workspace. This adds a second route into the existing
 // FOF kernels; the kernels themselves are unchanged.
-#include <mutex>
-
 #include "vr_internal.cuh"
 #include "vr_workspace.h"
 
@@ -12,24 +10,12 @@ namespace {
 // Scratch shared by every call on a device (held by the device until the process exits).
 static __device__ __align__(256) unsigned char g_fof3d_scratch[VR_FOF3D_NOALLOC_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void *g_scratch_addr[kMaxDevices] = {nullptr};
-
-// Device address of the static array on the current device; looked up once per device.
-// In host code the array's name is only a stand-in, so the kernels must be given this
-// address, never the symbol itself.
-cudaError_t scratch_address(int dev, void **out) {
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_addr[dev]) {
-    void *p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_fof3d_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = p;
-  }
-  *out = g_scratch_addr[dev];
-  return cudaSuccess;
-}
+// Device address of the static array in the current context. It is looked up on every
+// call (no allocation, no synchronisation): a cached address would go stale if the
+// context were destroyed and created again (cudaDeviceReset reloads the module). In host
+// code the array's name is only a stand-in, so the kernels must be given this address,
+// never the symbol itself.
+cudaError_t scratch_address(void **out) { return cudaGetSymbolAddress(out, g_fof3d_scratch); }
 
 }  // namespace
 
@@ -40,9 +26,9 @@ extern "C" vr_status vr_fof3d_noalloc(const int32_t *pos, int64_t n, int64_t lin
   if (!pos || !label) return VR_ERR_INVALID_ARG;
   if (vr::ws_fof3d(n) > (size_t)VR_FOF3D_NOALLOC_BYTES) return VR_ERR_INVALID_ARG;
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return VR_ERR_CUDA;
+  if (cudaGetDevice(&dev) != cudaSuccess) return VR_ERR_CUDA;
   void *scratch = nullptr;
-  if (scratch_address(dev, &scratch) != cudaSuccess) return VR_ERR_CUDA;
+  if (scratch_address(&scratch) != cudaSuccess) return VR_ERR_CUDA;
   // A context on the stack: vr_fof3d uses it only for its error text and event timers
   // (off), so nothing is allocated here.
   vr_ctx local;

@@ -77,3 +77,20 @@ def test_context_needs_a_gpu():
         pytest.skip("a GPU is present")
     with pytest.raises(vr.VrError):
         vr.Context(0)
+
+
+def test_noalloc_scratch_fits_the_stated_maximum():
+    """The 3D FOF scratch for n = VR_FOF3D_NOALLOC_MAX_N fits the static array of
+    VR_FOF3D_NOALLOC_BYTES (host-side size function of the library; no GPU needed), so
+    every n up to the stated maximum is accepted."""
+    src = open(os.path.join(ROOT, "include", "vr.h")).read()
+    max_n = int(re.search(r"#define VR_FOF3D_NOALLOC_MAX_N (\d+)", src).group(1))
+    m = re.search(r"#define VR_FOF3D_NOALLOC_BYTES \((\d+)u << (\d+)\)", src)
+    nbytes = int(m.group(1)) << int(m.group(2))
+    L = ctypes.CDLL(_build.build())
+    ws = getattr(L, "_ZN2vr8ws_fof3dEl")  # size_t vr::ws_fof3d(int64_t)
+    ws.restype = ctypes.c_size_t
+    ws.argtypes = [ctypes.c_int64]
+    need = ws(max_n)
+    assert 0 < need <= nbytes, (need, nbytes)
+    assert ws(max_n + 1) >= need  # the size grows with n
