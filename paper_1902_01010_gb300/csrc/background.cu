@@ -759,12 +759,15 @@ __global__ void k_ratio(const uint32_t *__restrict__ hid, const uint32_t *__rest
                         int64_t m0, int64_t m1, const int4 *__restrict__ u, const float4 *__restrict__ v,
                         const float *__restrict__ f_l, const CellNode *__restrict__ nodes,
                         const double *__restrict__ mom, const uint32_t *__restrict__ leaf_of,
-                        float *__restrict__ R, unsigned long long *__restrict__ ndegen) {
+                        float *__restrict__ R, unsigned long long *__restrict__ ndegen,
+                        const uint32_t *__restrict__ hoff, uint32_t szlo, uint32_t szhi) {
   int64_t m = m0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // members [m0, m1)
   if (m >= m1) return;
   const uint32_t h = hid[m];
   const uint32_t base = nodeoff[h];
   if (nodeoff[h + 1] == base) return;  // halo not searched
+  const uint32_t nh = hoff[h + 1] - hoff[h];
+  if (nh <= szlo || nh > szhi) return;  // another launch's halo
   const int4 p = u[m];
   const float4 q = v[m];
   const uint32_t own = leaf_of[m];
@@ -788,12 +791,12 @@ __global__ void k_ratio(const uint32_t *__restrict__ hid, const uint32_t *__rest
   for (int k = 0; k < nc; ++k) {
     const double *c = mom + 13 * (int64_t)cells[k];
     double dx = (double)p.x - c[1], dy = (double)p.y - c[2], dz = (double)p.z - c[3];
-    double r = sqrt(dx * dx + dy * dy + dz * dz);
-    if (r == 0.0) {
+    const double d2 = dx * dx + dy * dy + dz * dz;
+    if (d2 == 0.0) {
       zero = k;
       break;
     }
-    w[k] = 1.0 / r;
+    w[k] = rsqrt(d2);  // 1 / |x - xbar|
   }
   double vb[3] = {0, 0, 0}, sg[6] = {0, 0, 0, 0, 0, 0};
   if (zero >= 0) {
@@ -823,7 +826,7 @@ __global__ void k_ratio(const uint32_t *__restrict__ hid, const uint32_t *__rest
   double y2 = (d2 - L[3] * y0 - L[4] * y1) / L[5];
   double qf = y0 * y0 + y1 * y1 + y2 * y2;
   const double ln2pi = 1.8378770664093453;  // ln(2 pi)
-  double lnfbg = -0.5 * qf - 1.5 * ln2pi - (log(L[0]) + log(L[2]) + log(L[5]));
+  double lnfbg = -0.5 * qf - 1.5 * ln2pi - log(L[0] * L[2] * L[5]);  // ln det L
   R[pidx] = (float)(log((double)f_l[pidx]) - lnfbg);
 }
 
@@ -915,7 +918,8 @@ vr_status run_background(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Aren
       const int64_t a = hoff_host[h], z = hoff_host[h + 1];
       if (z - a < p->nsearch_min) continue;
       k_ratio<<<grid_for(z - a, 256), 256, 0, s>>>(g.hid, bg.nodeoff, a, z, g.u, g.v, f_l, bg.nodes,
-                                                  bg.mom, bg.leaf_of, R, ndeg);
+                                                  bg.mom, bg.leaf_of, R, ndeg, g.hoff, 0u,
+                                                  0xffffffffu);
       VR_LAUNCHED(ctx, "k_ratio");
     }
     return VR_OK;
@@ -938,11 +942,11 @@ vr_status run_background(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Aren
 }
 
 vr_status background_ratio(vr_ctx *ctx, const HaloSeg &g, const Background &bg, const float *f_l,
-                           float *R, cudaStream_t s) {
+                           float *R, cudaStream_t s, uint32_t szlo, uint32_t szhi) {
   if (g.H == 0) return VR_OK;
   unsigned long long *ndeg = (unsigned long long *)&ctx->d_status->info[0];
   VR_TIMED(ctx, "ratio", s, k_ratio<<<grid_for(g.NHP, 256), 256, 0, s>>>(g.hid, bg.nodeoff, 0, g.NHP, g.u, g.v, f_l, bg.nodes,
-                                               bg.mom, bg.leaf_of, R, ndeg));
+                                               bg.mom, bg.leaf_of, R, ndeg, g.hoff, szlo, szhi));
   VR_LAUNCHED(ctx, "k_ratio");
   return VR_OK;
 }

@@ -32,6 +32,8 @@ size_t background_bytes(int64_t n, const vr_params *p);
 vr_status run_background(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Arena &ar,
                          const float *f_l, float *R, double *halo_stats, Background *out,
                          cudaStream_t s, const uint32_t *hoff_host = nullptr);
+// R of the members of halos with szlo < N_H <= szhi.
 vr_status background_ratio(vr_ctx *ctx, const HaloSeg &g, const Background &bg, const float *f_l,
-                           float *R, cudaStream_t s);
+                           float *R, cudaStream_t s, uint32_t szlo = 0,
+                           uint32_t szhi = 0xffffffffu);
 }  // namespace vr

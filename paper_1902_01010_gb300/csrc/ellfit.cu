@@ -152,11 +152,15 @@ __device__ bool solve4(const double *jj, double lambda, const double *b, double 
   return true;
 }
 
-// R of every halo slot, in slot order (the selections below read it many times).
+// R of every slot of the halos with szlo < N_H <= szhi, in slot order (the selections
+// below read it many times).
 __global__ void k_gather_r(const float4 *__restrict__ v, const float *__restrict__ R, int64_t nhp,
-                           float *__restrict__ Rs) {
+                           const uint32_t *__restrict__ hid, const uint32_t *__restrict__ hoff,
+                           uint32_t szlo, uint32_t szhi, float *__restrict__ Rs) {
   const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (m < nhp) Rs[m] = R[__float_as_int(v[m].w)];
+  if (m >= nhp) return;
+  const uint32_t h = hid[m], nh = hoff[h + 1] - hoff[h];
+  if (nh > szlo && nh <= szhi) Rs[m] = R[__float_as_int(v[m].w)];
 }
 
 // The key of rank k - 1 given the key `a` of rank k (0-based, k >= 1) among the valid
@@ -196,7 +200,8 @@ __global__ void __launch_bounds__(kFT, VR_FIT_MINB) k_ell_fit(const uint32_t *__
                                                  const float4 *__restrict__ v,
                                                  const float *__restrict__ Rs, int nb_min,
                                                  int nb_max, int iters, double *__restrict__ hs,
-                                                 float *__restrict__ ell) {
+                                                 float *__restrict__ ell, uint32_t szlo,
+                                                 uint32_t szhi) {
   __shared__ uint32_t s_dig[256];
   __shared__ uint32_t s_scan[256];
   __shared__ unsigned long long s_pre;
@@ -211,6 +216,7 @@ __global__ void __launch_bounds__(kFT, VR_FIT_MINB) k_ell_fit(const uint32_t *__
   if (nodeoff[h + 1] == nodeoff[h]) return;  // not searched
   const uint32_t hb = hoff[h], he = hoff[h + 1];
   const int nh = (int)(he - hb);
+  if (he - hb <= szlo || he - hb > szhi) return;  // another launch's halo
   const int t = threadIdx.x;
   auto rval = [&](int i) { return Rs[hb + i]; };
   // number of finite values
@@ -370,12 +376,14 @@ __global__ void __launch_bounds__(kFT, VR_FIT_MINB) k_ell_fit(const uint32_t *__
 }
 
 vr_status run_fit(vr_ctx *ctx, const HaloSeg &g, const Background &bg, const vr_params *p,
-                  const float *R, double *halo_stats, float *ell, cudaStream_t s, const uint32_t *hoff_host) {
+                  const float *R, double *halo_stats, float *ell, cudaStream_t s, const uint32_t *hoff_host,
+                  uint32_t szlo, uint32_t szhi) {
   if (g.H == 0) return VR_OK;
   if (p->fit_nbins_max > kMaxFitBins)
     return set_error(ctx, VR_ERR_INVALID_ARG, "fit_nbins_max above %d", kMaxFitBins);
   float *Rs = reinterpret_cast<float *>(g.scratch_u32_a);  // [n + 1] words, unused here
-  k_gather_r<<<grid_for(g.NHP, 256), 256, 0, s>>>(g.v, R, g.NHP, Rs);
+  if (hoff_host) szlo = 0, szhi = 0xffffffffu;
+  k_gather_r<<<grid_for(g.NHP, 256), 256, 0, s>>>(g.v, R, g.NHP, g.hid, g.hoff, szlo, szhi, Rs);
   VR_LAUNCHED(ctx, "k_gather_r");
   if (hoff_host) {  // one launch per searched halo, in the size order
     std::vector<uint32_t> ord(g.H);
@@ -384,14 +392,15 @@ vr_status run_fit(vr_ctx *ctx, const HaloSeg &g, const Background &bg, const vr_
     for (int64_t i = 0; i < g.H; ++i) {
       if (hoff_host[ord[i] + 1] - hoff_host[ord[i]] < (uint32_t)p->nsearch_min) continue;
       k_ell_fit<<<1, kFT, 0, s>>>(g.hoff, g.horder, bg.nodeoff, i, i + 1, g.v, Rs, p->fit_nbins_min,
-                                  p->fit_nbins_max, p->fit_iters, halo_stats, ell);
+                                  p->fit_nbins_max, p->fit_iters, halo_stats, ell, 0u, 0xffffffffu);
       VR_LAUNCHED(ctx, "k_ell_fit");
     }
     return VR_OK;
   }
   VR_TIMED(ctx, "ell_fit", s, k_ell_fit<<<(unsigned)g.H, kFT, 0, s>>>(g.hoff, g.horder, bg.nodeoff, 0, g.H, g.v, Rs,
                                                                        p->fit_nbins_min, p->fit_nbins_max,
-                                                                       p->fit_iters, halo_stats, ell));
+                                                                       p->fit_iters, halo_stats, ell, szlo,
+                                                                       szhi));
   VR_LAUNCHED(ctx, "k_ell_fit");
   return VR_OK;
 }

@@ -5,14 +5,19 @@
 
 namespace vr {
 size_t velden_bytes(int64_t n, int nmin, int nse);
-// hoff_host / plain: non-NULL / true selects one launch per halo (the plain form)
+// hoff_host / plain: non-NULL / true selects one launch per halo (the plain form).
+// ev_big (batched form): recorded on s once the f_l of every halo above kVBinEdge0
+// members is written.
 vr_status run_velden(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Arena &ar, float *f_l,
-                     cudaStream_t s, const uint32_t *hoff_host = nullptr);
+                     cudaStream_t s, const uint32_t *hoff_host = nullptr,
+                     cudaEvent_t ev_big = nullptr);
 vr_status fill_f32(vr_ctx *ctx, float *a, int64_t n, float val, cudaStream_t s);
 vr_status fill_i32(vr_ctx *ctx, int32_t *a, int64_t n, int32_t val, cudaStream_t s);
+// Batched form: halos of szlo < N_H <= szhi only.
 vr_status run_fit(vr_ctx *ctx, const HaloSeg &g, const Background &bg, const vr_params *p,
                   const float *R, double *halo_stats, float *ell, cudaStream_t s,
-                  const uint32_t *hoff_host = nullptr);
+                  const uint32_t *hoff_host = nullptr, uint32_t szlo = 0,
+                  uint32_t szhi = 0xffffffffu);
 size_t fof6d_bytes(int64_t n, int nmin);
 // Halo table rows (label, N_H, frame, sigma_v) for every halo, one CTA per halo.
 vr_status run_halo_frame(vr_ctx *ctx, const HaloSeg &g, int nsearch_min, double *halo_stats,

@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "stages.h"
+#include "tuning.cuh"
 #include "vr_workspace.h"
 
 namespace vr {
@@ -335,11 +336,23 @@ vr_status vr_find_substructure(vr_ctx *ctx, const int32_t *pos, const float *vel
     if ((st = run_background(ctx, g, p, ar, nullptr, R, halo_stats, &bg, ctx->side2)) != VR_OK)
       return st;
     VR_CUDA(ctx, cudaEventRecord(ctx->ev_join2, ctx->side2));
-    if ((st = run_velden(ctx, g, p, ar, f_l, s)) != VR_OK) return st;
+    if ((st = run_velden(ctx, g, p, ar, f_l, s, nullptr, ctx->ev_flbig)) != VR_OK) return st;
+    // R and the fit of the halos above kVBinEdge0 members (the first f_l launch) run on
+    // the side stream while the f_l kernels of the smaller halos finish on s; the two
+    // halves write disjoint halos and members
+    const uint32_t edge = kVBinEdge0, all = 0xffffffffu;
+    VR_CUDA(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_flbig, 0));
+    VR_CUDA(ctx, cudaStreamWaitEvent(ctx->side, ctx->ev_join2, 0));
+    if ((st = background_ratio(ctx, g, bg, f_l, R, ctx->side, edge, all)) != VR_OK) return st;
+    if ((st = run_fit(ctx, g, bg, p, R, halo_stats, ell, ctx->side, nullptr, edge, all)) != VR_OK)
+      return st;
+    VR_CUDA(ctx, cudaEventRecord(ctx->ev_tail, ctx->side));
     VR_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev_join2, 0));
-    if ((st = background_ratio(ctx, g, bg, f_l, R, s)) != VR_OK) return st;
+    if ((st = background_ratio(ctx, g, bg, f_l, R, s, 0u, edge)) != VR_OK) return st;
+    if ((st = run_fit(ctx, g, bg, p, R, halo_stats, ell, s, nullptr, 0u, edge)) != VR_OK) return st;
+    VR_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev_tail, 0));
   }
-  if ((st = run_fit(ctx, g, bg, p, R, halo_stats, ell, s, hh)) != VR_OK) return st;
+  if (plain && (st = run_fit(ctx, g, bg, p, R, halo_stats, ell, s, hh)) != VR_OK) return st;
   ar.off = mark;
   if (g.H > 0) {
     k_link_lengths<<<grid_for(g.H, 256), 256, 0, s>>>(halo_stats, g.H, lx_sub, alpha_lv);

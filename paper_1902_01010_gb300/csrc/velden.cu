@@ -696,8 +696,11 @@ void *big_kernel(int shape) {
 // Runs the f_l stage on an existing segmentation; f_l must already hold NaN outside
 // halos.
 vr_status run_velden(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Arena &ar, float *f_l,
-                     cudaStream_t s, const uint32_t *hoff_host) {
-  if (g.H == 0) return VR_OK;
+                     cudaStream_t s, const uint32_t *hoff_host, cudaEvent_t ev_big) {
+  if (g.H == 0) {
+    if (ev_big) VR_CUDA(ctx, cudaEventRecord(ev_big, s));
+    return VR_OK;
+  }
   const int64_t H = g.H;
   int64_t hmax = g.n / (p->nmin > 0 ? p->nmin : 1) + 2;
   int64_t nbmax = bucket_bound(g.n, p->nse);
@@ -743,7 +746,10 @@ vr_status run_velden(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Arena &a
   uint32_t nsb = 0, eg[2] = {0, 0};
   memcpy(&nsb, ctx->h_pinned + 34, 4);
   memcpy(eg, ctx->h_pinned + 35, 8);
-  if (nsb == 0) return VR_OK;
+  if (nsb == 0) {
+    if (ev_big) VR_CUDA(ctx, cudaEventRecord(ev_big, s));
+    return VR_OK;
+  }
   int64_t nbpad = 32LL * nsb;
   k_sb_fill<<<grid_for(H, T), T, 0, s>>>(sbr, g.horder, H, sbs, sbe, sbhalo);
   VR_LAUNCHED(ctx, "k_sb_fill");
@@ -786,7 +792,10 @@ vr_status run_velden(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Arena &a
   const int64_t hi[kVBins] = {32LL * eg[0], 32LL * eg[1], nbpad};
   timer_begin(ctx, "velden_big", s);
   for (int k = 0; k < kVBins; ++k) {
-    if (hi[k] <= lo[k]) continue;
+    if (hi[k] <= lo[k]) {
+      if (k == 0 && ev_big) VR_CUDA(ctx, cudaEventRecord(ev_big, s));
+      continue;
+    }
     if (p->nv <= 32 && vmeasure(ctx, k)) {
       Tuning *tn = ctx->tune;
       cudaEvent_t e0, e1;
@@ -812,6 +821,7 @@ vr_status run_velden(vr_ctx *ctx, const HaloSeg &g, const vr_params *p, Arena &a
       VR_CUDA(ctx, big(p->nv <= 32 ? vshape_for(ctx, k) : 0, lo[k], hi[k]));
       VR_LAUNCHED(ctx, "k_velden_big");
     }
+    if (k == 0 && ev_big) VR_CUDA(ctx, cudaEventRecord(ev_big, s));  // halos > kVBinEdge0 done
   }
   timer_end(ctx, "velden_big", s);
   return VR_OK;

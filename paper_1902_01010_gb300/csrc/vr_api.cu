@@ -194,7 +194,9 @@ vr_status vr_create(vr_ctx **out, int device) {
       cudaEventCreateWithFlags(&c->ev_fork2, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_flbig, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_tail, cudaEventDisableTiming) != cudaSuccess) {
     vr_destroy(c);
     return VR_ERR_CUDA;
   }
@@ -212,6 +214,8 @@ void vr_destroy(vr_ctx *ctx) {
   if (ctx->ev_join2) cudaEventDestroy(ctx->ev_join2);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->ev_flbig) cudaEventDestroy(ctx->ev_flbig);
+  if (ctx->ev_tail) cudaEventDestroy(ctx->ev_tail);
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
   free(ctx);

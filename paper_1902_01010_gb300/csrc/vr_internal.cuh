@@ -42,6 +42,7 @@ struct vr_ctx {
   cudaEvent_t ev_fork, ev_join;
   cudaStream_t side2;       // third stream: the cell-tree build beside the f_l stage
   cudaEvent_t ev_fork2, ev_join2;
+  cudaEvent_t ev_flbig, ev_tail;  // f_l of the largest halos done; their R and fit done
 };
 
 namespace vr {
