@@ -96,6 +96,13 @@ void vr_destroy(vr_ctx *ctx);
 /* Last error message of ctx (empty string if none). Owned by ctx. */
 const char *vr_last_error(const vr_ctx *ctx);
 
+/* Host-side logging of ctx to stderr (the paper's code has a verbosity flag; the levels
+ * here are this library's own): 0 = silent (the default), 1 = every error as it is
+ * recorded (the text vr_last_error returns, prefixed "vr: "), 2 = also one line per
+ * vr_fof3d / vr_find_substructure call with n and its status. Returns VR_ERR_INVALID_ARG
+ * for a NULL ctx or a level outside [0, 2]. */
+vr_status vr_set_log_level(vr_ctx *ctx, int level);
+
 /* Bytes of workspace needed by any call below for n particles with parameters p
  * (p may be NULL for defaults). */
 vr_status vr_workspace_size(vr_ctx *ctx, int64_t n, const vr_params *p, size_t *bytes);

@@ -629,5 +629,5 @@ extern "C" vr_status vr_fof3d(vr_ctx *ctx, const int32_t *pos, int64_t n, int64_
   VR_LAUNCHED(ctx, "k_fof_roots");
   k_fof_label<<<grid_for(n, T), T, 0, s>>>(B.parent, B.posS, B.minidx, n, label);
   VR_LAUNCHED(ctx, "k_fof_label");
-  return VR_OK;
+  return log_call(ctx, "vr_fof3d", n, VR_OK);
 }

@@ -360,7 +360,7 @@ vr_status vr_find_substructure(vr_ctx *ctx, const int32_t *pos, const float *vel
   }
   if ((st = run_fof6d(ctx, g, p, ar, ell, halo_stats, g.H, label6, s, plain)) != VR_OK) return st;
   if (nhalo) *nhalo = g.H;
-  return read_status(ctx, s, nullptr);
+  return log_call(ctx, "vr_find_substructure", n, read_status(ctx, s, nullptr));
 }
 
 }  // extern "C"

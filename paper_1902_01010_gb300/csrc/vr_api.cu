@@ -1,6 +1,7 @@
 // Context, parameters, errors and workspace sizing of the C ABI.
 #include <math.h>
 #include <stdarg.h>
+#include <stdio.h>
 #include <stdlib.h>
 
 #include <atomic>
@@ -86,12 +87,19 @@ vr_status set_error(vr_ctx *ctx, vr_status st, const char *fmt, ...) {
     va_start(ap, fmt);
     vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
     va_end(ap);
+    if (ctx->log_level >= 1) fprintf(stderr, "vr: %s (status %d)\n", ctx->err, (int)st);
   }
   return st;
 }
 
 vr_status check_cuda(vr_ctx *ctx, cudaError_t e, const char *what) {
   return set_error(ctx, VR_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+vr_status log_call(vr_ctx *ctx, const char *name, int64_t n, vr_status st) {
+  if (ctx && ctx->log_level >= 2)
+    fprintf(stderr, "vr: %s n=%lld status %d\n", name, (long long)n, (int)st);
+  return st;
 }
 
 vr_status params_check(vr_ctx *ctx, const vr_params *p) {
@@ -222,6 +230,12 @@ void vr_destroy(vr_ctx *ctx) {
 }
 
 const char *vr_last_error(const vr_ctx *ctx) { return ctx ? ctx->err : "no context"; }
+
+vr_status vr_set_log_level(vr_ctx *ctx, int level) {
+  if (!ctx || level < 0 || level > 2) return VR_ERR_INVALID_ARG;
+  ctx->log_level = level;
+  return VR_OK;
+}
 
 vr_status vr_sync(vr_ctx *ctx, void *stream) {
   if (!ctx) return VR_ERR_INVALID_ARG;

@@ -43,6 +43,7 @@ struct vr_ctx {
   cudaStream_t side2;       // third stream: the cell-tree build beside the f_l stage
   cudaEvent_t ev_fork2, ev_join2;
   cudaEvent_t ev_flbig, ev_tail;  // f_l of the largest halos done; their R and fit done
+  int log_level;            // vr_set_log_level: 0 silent, 1 errors, 2 errors and calls
 };
 
 namespace vr {
@@ -50,6 +51,8 @@ namespace vr {
 // ------------------------------------------------------------------ errors
 vr_status set_error(vr_ctx *ctx, vr_status st, const char *fmt, ...);
 vr_status check_cuda(vr_ctx *ctx, cudaError_t e, const char *what);
+// Level-2 log line of an entry point's call (vr_set_log_level); returns st.
+vr_status log_call(vr_ctx *ctx, const char *name, int64_t n, vr_status st);
 #define VR_CUDA(ctx, call)                                    \
   do {                                                        \
     cudaError_t _e = (call);                                  \

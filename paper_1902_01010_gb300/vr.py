@@ -28,7 +28,7 @@ EXPORTS = ("vr_params_default", "vr_create", "vr_destroy", "vr_last_error", "vr_
            "vr_fof6d_field", "vr_clean_groups", "vr_grow_params_default", "vr_grow_groups",
            "vr_core_params_default", "vr_core_search", "vr_core_grow_params_default",
            "vr_core_grow", "vr_find_substructure", "vr_autotune", "vr_tuning_force",
-           "vr_tuning_report")
+           "vr_tuning_report", "vr_set_log_level")
 
 
 class VrError(RuntimeError):
@@ -218,6 +218,11 @@ class Context:
 
     def sync(self, stream=None):
         self.check(lib().vr_sync(self.h, _stream(stream)))
+
+    def log_level(self, level: int):
+        """stderr logging of this context: 0 silent, 1 errors, 2 errors and one line per
+        3D FOF or substructure call (vr_set_log_level)."""
+        self.check(lib().vr_set_log_level(self.h, int(level)))
 
     # ------------------------------------------------------------ launch shapes
     def autotune(self, enable: bool = True):

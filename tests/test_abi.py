@@ -94,3 +94,13 @@ def test_noalloc_scratch_fits_the_stated_maximum():
     need = ws(max_n)
     assert 0 < need <= nbytes, (need, nbytes)
     assert ws(max_n + 1) >= need  # the size grows with n
+
+
+def test_log_level_rejects_bad_arguments_without_a_gpu():
+    """vr_set_log_level needs a context: NULL (and so any call made here, without a GPU)
+    returns VR_ERR_INVALID_ARG instead of touching memory."""
+    L = ctypes.CDLL(_build.build())
+    f = L.vr_set_log_level
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    assert f(None, 1) == 1 and f(None, 0) == 1

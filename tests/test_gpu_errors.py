@@ -166,3 +166,31 @@ def test_two_stage_link_table_full(ctx, reference):
         ctx.sync()
     assert e.value.code == VR_ERR_UNSUPPORTED and "link-count table" in str(e.value)
     _still_works(ctx, reference)
+
+
+def test_log_levels(ctx, reference, capfd):
+    """vr_set_log_level: level 2 prints one line per 3D FOF / substructure call, level 1
+    prints an error as it is recorded, level 0 prints nothing; results are unchanged."""
+    box = reference[0]
+    pos = torch.from_numpy(box.pos).cuda()
+    capfd.readouterr()
+    ctx.log_level(2)
+    lab = ctx.fof3d(pos, box.link_d2)
+    ctx.sync()
+    err = capfd.readouterr().err
+    assert f"vr: vr_fof3d n={box.n} status 0" in err
+    assert np.array_equal(lab.cpu().numpy(), reference[1])
+    ctx.log_level(1)
+    with pytest.raises(Exception):
+        ctx.fof3d(pos, 0)  # link_d2 below 1
+    err = capfd.readouterr().err
+    assert "vr: link_d2 must be in" in err and "vr_fof3d n=" not in err
+    ctx.log_level(0)
+    with pytest.raises(Exception):
+        ctx.fof3d(pos, 0)
+    assert capfd.readouterr().err == ""
+    from paper_1902_01010_gb300 import VrError
+
+    with pytest.raises(VrError):
+        ctx.log_level(3)
+    _still_works(ctx, reference)
